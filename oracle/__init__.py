@@ -1,0 +1,296 @@
+"""FP64 CPU oracle for the spectral node-aggregation path (arXiv 1812.08942,
+Sec. 3.2 Phase A and Alg. 3).
+
+TEST INFRASTRUCTURE ONLY.  This package is the plain, slow reference that the
+CUDA library is checked against.  Only the test suite, ``__graft_entry__.smoke()``
+and the CPU-baseline leg of ``bench.py`` may import it; the library itself
+never does, and the two share no code.  The arithmetic lives in ``oracle.c``
+(plain C, binary64, single thread, built with ``-ffp-contract=off``); this
+module only marshals numpy arrays into it, runs the level loop, and holds the
+eigenvalue checks (numpy / scipy FP64 solvers).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so beside it (gcc, -O2, no fast-math)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call([
+            "gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+            "-fno-fast-math", "-Wall", "-Wno-unused-function", _SRC, "-o", tmp, "-lm",
+        ])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    build()
+    lib = ctypes.CDLL(_LIB)
+    P = ctypes.c_void_p
+    I64 = ctypes.c_int64
+    I = ctypes.c_int
+    D = ctypes.c_double
+    U64 = ctypes.c_uint64
+    sig = {
+        "oracle_degrees": (I, [I64, I64, P, P, P, P]),
+        "oracle_laplacian_apply": (I, [I64, I64, P, P, P, I, P, P]),
+        "oracle_splitmix64": (U64, [U64, U64]),
+        "oracle_test_vectors_raw": (None, [I64, I, U64, I, P]),
+        "oracle_center_normalize": (None, [I64, I, P]),
+        "oracle_jacobi_sweep": (I, [I64, I64, P, P, P, P, I, D, P, P]),
+        "oracle_smooth": (I, [I64, I64, P, P, P, I, I, D, U64, I, P]),
+        "oracle_affinity": (I, [I64, I64, P, P, I, P, P, P]),
+        "oracle_aggregate": (I, [I64, I64, P, P, P, I64, I, P, P, P]),
+        "oracle_coarsen": (I, [I64, I64, P, P, P, P, I64, P, P, P, P]),
+        "oracle_loss": (I, [I64, I64, P, P, P, I64, I64, P, P, P, P, I, P, I, D, P, P, P, P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _check(st, what):
+    if st != 0:
+        raise ValueError("oracle %s failed with status %d" % (what, st))
+
+
+# --------------------------------------------------------------------------
+# Graph primitives (Sec. 2.1)
+# --------------------------------------------------------------------------
+def degrees(n, u, v, w):
+    u, v, w = _i32(u), _i32(v), _f64(w)
+    deg = np.empty(n, np.float64)
+    _check(_load().oracle_degrees(n, len(u), _p(u), _p(v), _p(w), _p(deg)), "degrees")
+    return deg
+
+
+def laplacian_apply(n, u, v, w, X):
+    """L X for an n x K block (or a length-n vector)."""
+    u, v, w = _i32(u), _i32(v), _f64(w)
+    X = _f64(X)
+    vec = X.ndim == 1
+    Xb = X.reshape(n, -1)
+    K = Xb.shape[1]
+    Y = np.empty_like(Xb)
+    _check(_load().oracle_laplacian_apply(n, len(u), _p(u), _p(v), _p(w), K, _p(Xb), _p(Y)), "L apply")
+    return Y.reshape(-1) if vec else Y
+
+
+def dense_laplacian(n, u, v, w):
+    """L as a dense matrix, column by column through ``laplacian_apply``."""
+    return laplacian_apply(n, u, v, w, np.eye(n))
+
+
+# --------------------------------------------------------------------------
+# Test vectors and smoothing (Sec. 3.2.1, Alg. 3)
+# --------------------------------------------------------------------------
+def splitmix64(seed: int, c: int) -> int:
+    return int(_load().oracle_splitmix64(seed, c))
+
+
+def test_vectors_raw(n, K, seed=0, level=0):
+    X = np.empty((n, K), np.float64)
+    _load().oracle_test_vectors_raw(n, K, seed, level, _p(X))
+    return X
+
+
+def center_normalize(X):
+    X = _f64(X).copy()
+    n, K = X.shape
+    _load().oracle_center_normalize(n, K, _p(X))
+    return X
+
+
+def jacobi_sweep(n, u, v, w, X, omega):
+    """One raw weighted-Jacobi sweep of Alg. 3 (no centring / normalising)."""
+    u, v, w = _i32(u), _i32(v), _f64(w)
+    X = _f64(X)
+    K = X.shape[1]
+    deg = degrees(n, u, v, w)
+    Y = np.empty_like(X)
+    _check(_load().oracle_jacobi_sweep(n, len(u), _p(u), _p(v), _p(w), _p(deg), K, omega, _p(X), _p(Y)), "sweep")
+    return Y
+
+
+def smooth(n, u, v, w, K, sweeps, omega=0.7, seed=0, level=0):
+    u, v, w = _i32(u), _i32(v), _f64(w)
+    X = np.empty((n, K), np.float64)
+    _check(_load().oracle_smooth(n, len(u), _p(u), _p(v), _p(w), K, sweeps, omega, seed, level, _p(X)), "smooth")
+    return X
+
+
+# --------------------------------------------------------------------------
+# Affinity / algebraic distance (Eq. eqn:agg, Sec. 3.2.2)
+# --------------------------------------------------------------------------
+def affinity(n, u, v, X, want_a=False):
+    u, v = _i32(u), _i32(v)
+    X = _f64(X)
+    K = X.shape[1]
+    m = len(u)
+    d = np.empty(m, np.float64)
+    a = np.empty(m, np.float64) if want_a else None
+    _check(_load().oracle_affinity(n, m, _p(u), _p(v), K, _p(X), _p(d), _p(a)), "affinity")
+    return (d, a) if want_a else d
+
+
+# --------------------------------------------------------------------------
+# Aggregation (Sec. 3.2.2) and Galerkin coarsening (L_R = H_G^R L_G H_R^G)
+# --------------------------------------------------------------------------
+def aggregate(n, u, v, d, target_nc, passes=2):
+    u, v, d = _i32(u), _i32(v), _f64(d)
+    agg = np.empty(n, np.int32)
+    nc = ctypes.c_int64(0)
+    merges = np.zeros(max(passes, 1), np.int64)
+    _check(_load().oracle_aggregate(n, len(u), _p(u), _p(v), _p(d), int(target_nc), passes,
+                                    _p(agg), ctypes.byref(nc), _p(merges)), "aggregate")
+    return agg, int(nc.value)
+
+
+def coarsen(n, u, v, w, agg, nc):
+    u, v, w, agg = _i32(u), _i32(v), _f64(w), _i32(agg)
+    m = len(u)
+    uc = np.empty(max(m, 1), np.int32)
+    vc = np.empty(max(m, 1), np.int32)
+    wc = np.empty(max(m, 1), np.float64)
+    mc = ctypes.c_int64(0)
+    _check(_load().oracle_coarsen(n, m, _p(u), _p(v), _p(w), _p(agg), int(nc), ctypes.byref(mc),
+                                  _p(uc), _p(vc), _p(wc)), "coarsen")
+    k = int(mc.value)
+    return uc[:k].copy(), vc[:k].copy(), wc[:k].copy()
+
+
+# --------------------------------------------------------------------------
+# Spectral-mismatch loss and its hand-derived gradient
+# --------------------------------------------------------------------------
+def loss(n, u, v, w, nc, uc, vc, wc, agg, X, sweeps, omega=0.7, want_grad=True):
+    u, v, w = _i32(u), _i32(v), _f64(w)
+    uc, vc, wc, agg = _i32(uc), _i32(vc), _f64(wc), _i32(agg)
+    X = _f64(X)
+    K = X.shape[1]
+    out = ctypes.c_double(0.0)
+    g = np.empty(len(uc), np.float64) if want_grad else None
+    Rf = np.empty(K, np.float64)
+    Rc = np.empty(K, np.float64)
+    _check(_load().oracle_loss(n, len(u), _p(u), _p(v), _p(w), int(nc), len(uc), _p(uc), _p(vc), _p(wc),
+                               _p(agg), K, _p(X), sweeps, omega, ctypes.byref(out), _p(g), _p(Rf), _p(Rc)),
+           "loss")
+    return float(out.value), g, Rf, Rc
+
+
+# --------------------------------------------------------------------------
+# Level loop (the paper repeats Phase A level by level; Alg. 5 consumes the
+# hierarchy).  Per-level target max(ceil(n/4), final_target).
+# --------------------------------------------------------------------------
+@dataclass
+class Level:
+    n: int
+    m: int
+    agg: np.ndarray
+    nc: int
+    uc: np.ndarray
+    vc: np.ndarray
+    wc: np.ndarray
+    d: np.ndarray = field(repr=False, default=None)
+    X: np.ndarray = field(repr=False, default=None)
+
+
+def reduce_multilevel(n, u, v, w, K, sweeps, omega=0.7, seed=0, final_target=1, passes=2,
+                      max_levels=64, keep=False, level_ratio=4):
+    """Run smooth -> affinity -> aggregate -> coarsen until n <= final_target or
+    a level makes no progress.  Returns the list of Level records."""
+    levels = []
+    cu, cv, cw, cn = _i32(u), _i32(v), _f64(w), int(n)
+    for lvl in range(max_levels):
+        if cn <= final_target or len(cu) == 0:
+            break
+        X = smooth(cn, cu, cv, cw, K, sweeps, omega, seed, lvl)
+        d = affinity(cn, cu, cv, X)
+        target = max(-(-cn // level_ratio), final_target)
+        agg, nc = aggregate(cn, cu, cv, d, target, passes)
+        if nc == cn:
+            break
+        uc, vc, wc = coarsen(cn, cu, cv, cw, agg, nc)
+        levels.append(Level(cn, len(cu), agg, nc, uc, vc, wc, d if keep else None, X if keep else None))
+        cu, cv, cw, cn = uc, vc, wc, nc
+    return levels
+
+
+def compose_maps(levels):
+    """Fine-to-coarsest aggregate map: agg_L(...agg_1(i))."""
+    if not levels:
+        return None
+    out = levels[0].agg.astype(np.int64)
+    for lv in levels[1:]:
+        out = lv.agg[out].astype(np.int64)
+    return out.astype(np.int32)
+
+
+# --------------------------------------------------------------------------
+# Eigenvalue check (method of the paper's eigenvalue figure for fe_tooth):
+# the smallest nontrivial Laplacian eigenvalues, FP64 on the CPU.
+# --------------------------------------------------------------------------
+def n_components(n, u, v):
+    from scipy.sparse import coo_matrix
+    from scipy.sparse.csgraph import connected_components
+    A = coo_matrix((np.ones(len(u)), (np.asarray(u), np.asarray(v))), shape=(n, n))
+    return int(connected_components(A, directed=False)[0])
+
+
+def sparse_laplacian(n, u, v, w):
+    from scipy.sparse import coo_matrix
+    u = np.asarray(u, np.int64)
+    v = np.asarray(v, np.int64)
+    w = np.asarray(w, np.float64)
+    deg = degrees(n, u, v, w)
+    r = np.concatenate([u, v, np.arange(n)])
+    c = np.concatenate([v, u, np.arange(n)])
+    x = np.concatenate([-w, -w, deg])
+    return coo_matrix((x, (r, c)), shape=(n, n)).tocsc()
+
+
+def smallest_nontrivial_eigs(n, u, v, w, k=10, dense_max=8000):
+    """The k smallest eigenvalues after skipping one zero per connected
+    component.  Dense eigh when n <= dense_max, else shift-invert eigsh."""
+    c = n_components(n, u, v)
+    if n <= dense_max:
+        L = sparse_laplacian(n, u, v, w).toarray()
+        ev = np.linalg.eigvalsh(L)
+        return ev[c:c + k]
+    from scipy.sparse.linalg import eigsh
+    L = sparse_laplacian(n, u, v, w)
+    deg = np.asarray(L.diagonal())
+    sigma = -1e-3 * float(deg.mean())
+    ev = eigsh(L, k=k + c, sigma=sigma, which="LM", return_eigenvectors=False, tol=1e-12)
+    ev = np.sort(ev)
+    return ev[c:c + k]

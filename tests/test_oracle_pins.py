@@ -1,0 +1,537 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each check reaches the expected value by a route other than the oracle's own
+code: closed-form spectra, FFT diagonalisation of circulant operators, published
+generator outputs, dense brute force, an independent handshake matching, finite
+differences.  A dropped term, a wrong sign or index, or a transposed operand in
+the oracle fails at least one of them.
+"""
+import itertools
+import json
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from handshake_ref import handshake_aggregate
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+# ---------------------------------------------------------------------------
+# Laplacian (Sec. 2.1): L = D - A, zero row sums, closed-form spectra
+# ---------------------------------------------------------------------------
+def test_laplacian_zero_row_sums_and_structure(oracle_mod):
+    g = W.random_sparse(40, 120, seed=1)
+    L = oracle_mod.dense_laplacian(g.n, g.u, g.v, g.w)
+    assert np.allclose(L.sum(1), 0.0, atol=1e-13)
+    assert np.allclose(L, L.T, atol=0)
+    off = L - np.diag(np.diag(L))
+    assert (off <= 0).all()
+    # diagonal is the weighted degree: every weight counted at both endpoints
+    assert np.isclose(np.trace(L), 2.0 * g.w.sum())
+
+
+def test_laplacian_quadratic_form(oracle_mod):
+    g = W.random_sparse(50, 200, seed=2)
+    rng = np.random.default_rng(3)
+    x = rng.normal(size=g.n)
+    Lx = oracle_mod.laplacian_apply(g.n, g.u, g.v, g.w, x)
+    q = float(np.sum(g.w * (x[g.u] - x[g.v]) ** 2))
+    assert np.isclose(x @ Lx, q, rtol=1e-13)
+
+
+@pytest.mark.parametrize("n", [7, 16])
+def test_spectrum_path_cycle_complete_star(oracle_mod, n):
+    j = np.arange(n)
+    g = W.path(n)
+    ev = np.linalg.eigvalsh(oracle_mod.dense_laplacian(g.n, g.u, g.v, g.w))
+    assert np.allclose(ev, np.sort(4 * np.sin(np.pi * j / (2 * n)) ** 2), atol=1e-12)
+    g = W.cycle(n)
+    ev = np.linalg.eigvalsh(oracle_mod.dense_laplacian(g.n, g.u, g.v, g.w))
+    assert np.allclose(ev, np.sort(4 * np.sin(np.pi * j / n) ** 2), atol=1e-12)
+    g = W.complete(n, weight=1.5)
+    ev = np.linalg.eigvalsh(oracle_mod.dense_laplacian(g.n, g.u, g.v, g.w))
+    assert np.allclose(ev, [0.0] + [1.5 * n] * (n - 1), atol=1e-12)
+    g = W.star(n)
+    ev = np.linalg.eigvalsh(oracle_mod.dense_laplacian(g.n, g.u, g.v, g.w))
+    assert np.allclose(ev, [0.0] + [1.0] * (n - 2) + [float(n)], atol=1e-12)
+
+
+def test_spectrum_grid(oracle_mod):
+    a, b = 6, 5
+    g = W.grid2d(a, b)
+    ev = np.linalg.eigvalsh(oracle_mod.dense_laplacian(g.n, g.u, g.v, g.w))
+    i, j = np.meshgrid(np.arange(a), np.arange(b))
+    ref = np.sort((4 * np.sin(np.pi * i / (2 * a)) ** 2 + 4 * np.sin(np.pi * j / (2 * b)) ** 2).ravel())
+    assert np.allclose(ev, ref, atol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Test vectors (Sec. 3.2.1): SplitMix64 known answers, uniform on [-1, 1)
+# ---------------------------------------------------------------------------
+def test_splitmix64_known_answers(oracle_mod):
+    with open(os.path.join(GOLDEN, "splitmix64_seed0.json")) as f:
+        ref = json.load(f)
+    for c, hexval in enumerate(ref["outputs"]):
+        assert oracle_mod.splitmix64(0, c) == int(hexval, 16)
+
+
+def test_test_vectors_distribution(oracle_mod):
+    X = oracle_mod.test_vectors_raw(20000, 4, seed=0, level=0)
+    assert X.min() >= -1.0 and X.max() < 1.0
+    assert abs(X.mean()) < 5 * np.sqrt(1 / 3 / X.size)
+    assert abs(X.var() - 1 / 3) < 0.01
+    from scipy.stats import kstest
+    assert kstest(X.ravel(), "uniform", args=(-1, 2)).pvalue > 1e-4
+    # levels and seeds give different streams
+    assert not np.array_equal(X[:10], oracle_mod.test_vectors_raw(20000, 4, 0, 1)[:10])
+    assert not np.array_equal(X[:10], oracle_mod.test_vectors_raw(20000, 4, 1, 0)[:10])
+
+
+def test_center_normalize(oracle_mod):
+    X = oracle_mod.center_normalize(oracle_mod.test_vectors_raw(1000, 5, 7, 0))
+    assert np.all(np.abs(X.sum(0)) <= 1e-13 * np.sqrt(1000))
+    assert np.allclose((X * X).sum(0), 1.0, atol=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# Smoothing (Alg. 3): FFT-diagonalised circulant graphs, complete graph,
+# dense brute force, isolated nodes, invariants
+# ---------------------------------------------------------------------------
+def _normalize_center(Y):
+    Y = Y - Y.mean(0)
+    return Y / np.linalg.norm(Y, axis=0)
+
+
+@pytest.mark.parametrize("omega,S", [(0.7, 5), (0.5, 8), (0.9, 3)])
+def test_smooth_cycle_fft(oracle_mod, omega, S):
+    n, K = 64, 6
+    g = W.cycle(n, weight=2.5)
+    X0 = oracle_mod.center_normalize(oracle_mod.test_vectors_raw(n, K, 0, 0))
+    theta = 2 * np.pi * np.arange(n) / n
+    mu = (1 - omega) + omega * np.cos(theta)  # eigenvalues of J on the cycle
+    ref = np.real(np.fft.ifft(np.fft.fft(X0, axis=0) * (mu ** S)[:, None], axis=0))
+    ref = _normalize_center(ref)
+    X = oracle_mod.smooth(n, g.u, g.v, g.w, K, S, omega, 0, 0)
+    assert np.max(np.abs(X - ref)) < 1e-13
+
+
+def test_smooth_weighted_circulant_fft(oracle_mod):
+    n, K, omega, S = 40, 4, 0.7, 6
+    a, b = 0.3, 2.0
+    g = W.circulant(n, [(1, a), (2, b)])
+    X0 = oracle_mod.center_normalize(oracle_mod.test_vectors_raw(n, K, 5, 2))
+    th = 2 * np.pi * np.arange(n) / n
+    mu = (1 - omega) + omega * (2 * a * np.cos(th) + 2 * b * np.cos(2 * th)) / (2 * a + 2 * b)
+    ref = _normalize_center(np.real(np.fft.ifft(np.fft.fft(X0, axis=0) * (mu ** S)[:, None], axis=0)))
+    X = oracle_mod.smooth(n, g.u, g.v, g.w, K, S, omega, 5, 2)
+    assert np.max(np.abs(X - ref)) < 1e-13
+
+
+def test_smooth_torus_fft2(oracle_mod):
+    a, b, K, omega, S = 8, 6, 3, 0.7, 4
+    g = W.torus2d(a, b)
+    X0 = oracle_mod.center_normalize(oracle_mod.test_vectors_raw(a * b, K, 3, 0))
+    ti = 2 * np.pi * np.arange(a) / a
+    tj = 2 * np.pi * np.arange(b) / b
+    mu = (1 - omega) + omega * (np.cos(ti)[None, :] + np.cos(tj)[:, None]) / 2  # [j, i]
+    Xg = X0.reshape(b, a, K)
+    ref = np.real(np.fft.ifft2(np.fft.fft2(Xg, axes=(0, 1)) * (mu ** S)[:, :, None], axes=(0, 1)))
+    ref = _normalize_center(ref.reshape(a * b, K))
+    X = oracle_mod.smooth(a * b, g.u, g.v, g.w, K, S, omega, 3, 0)
+    assert np.max(np.abs(X - ref)) < 1e-13
+
+
+@pytest.mark.parametrize("n,omega,S", [(5, 0.7, 5), (3, 0.9, 3), (3, 0.9, 4)])
+def test_smooth_complete_graph(oracle_mod, n, omega, S):
+    # Sec. 3.2.3: on a complete graph smoothing cannot separate nodes.  For a
+    # centred x, D^-1 A x = -x/(n-1), so each sweep only rescales x.
+    g = W.complete(n)
+    K = 4
+    X0 = oracle_mod.center_normalize(oracle_mod.test_vectors_raw(n, K, 0, 0))
+    sign = np.sign(1 - omega - omega / (n - 1)) ** S
+    X = oracle_mod.smooth(n, g.u, g.v, g.w, K, S, omega, 0, 0)
+    assert np.max(np.abs(X - sign * X0)) < 1e-14
+
+
+def test_smooth_dense_bruteforce(oracle_mod):
+    g = W.random_sparse(30, 80, seed=11)
+    n, K, omega, S = g.n, 5, 0.65, 7
+    A = np.zeros((n, n))
+    A[g.u, g.v] = g.w
+    A[g.v, g.u] = g.w
+    J = (1 - omega) * np.eye(n) + omega * A / A.sum(1)[:, None]
+    X0 = oracle_mod.center_normalize(oracle_mod.test_vectors_raw(n, K, 9, 1))
+    ref = _normalize_center(np.linalg.matrix_power(J, S) @ X0)
+    X = oracle_mod.smooth(n, g.u, g.v, g.w, K, S, omega, 9, 1)
+    assert np.max(np.abs(X - ref)) < 1e-13
+
+
+def test_sweep_isolated_node_unchanged(oracle_mod):
+    # node 5 has no edges: the reading (D^-1 A x)_i := x_i keeps its row
+    u = np.array([0, 1, 2, 3], np.int32)
+    v = np.array([1, 2, 3, 4], np.int32)
+    w = np.ones(4)
+    X = np.arange(12, dtype=np.float64).reshape(6, 2) - 5.0
+    Y = oracle_mod.jacobi_sweep(6, u, v, w, X, 0.7)
+    assert np.array_equal(Y[5], X[5])
+    # an interior path node: (1-w) x_i + w (x_{i-1} + x_{i+1}) / 2
+    assert np.allclose(Y[2], 0.3 * X[2] + 0.7 * (X[1] + X[3]) / 2)
+
+
+def test_smooth_invariants_and_lowpass(oracle_mod):
+    g = W.grid2d(20, 20)
+    K = 8
+    Xprev = oracle_mod.center_normalize(oracle_mod.test_vectors_raw(g.n, K, 0, 0))
+    rq = []
+    for S in range(1, 6):
+        X = oracle_mod.smooth(g.n, g.u, g.v, g.w, K, S, 0.7, 0, 0)
+        assert np.all(np.abs(X.sum(0)) <= 1e-13 * np.sqrt(g.n))
+        assert np.allclose((X * X).sum(0), 1.0, atol=1e-14)
+        LX = oracle_mod.laplacian_apply(g.n, g.u, g.v, g.w, X)
+        rq.append(float(np.mean((X * LX).sum(0))))
+    # low-pass filter (Sec. 3.5): the Rayleigh quotient falls with every sweep
+    assert all(b < a for a, b in zip(rq, rq[1:]))
+
+
+# ---------------------------------------------------------------------------
+# Affinity and algebraic distance (Eq. eqn:agg, Sec. 3.2.2)
+# ---------------------------------------------------------------------------
+def test_affinity_hand_examples(oracle_mod):
+    X = np.array([[1.0, 0.0, 0.0],
+                  [1.0, 1.0, 0.0],    # cos^2 with row 0 = 1/2
+                  [2.0, 1.0, -2.0],   # orthogonal to row 3
+                  [1.0, 2.0, 2.0],
+                  [-3.0, -6.0, -6.0],  # parallel (opposite) to row 3
+                  [0.0, 0.0, 0.0]])   # zero row
+    u = np.array([0, 2, 3, 0], np.int32)
+    v = np.array([1, 3, 4, 5], np.int32)
+    d, a = oracle_mod.affinity(6, u, v, X, want_a=True)
+    assert np.allclose(a, [0.5, 0.0, 1.0, 0.0], atol=1e-15)
+    assert np.allclose(d, [0.5, 1.0, 0.0, 1.0], atol=1e-15)
+    assert d[2] == 0.0
+
+
+def test_affinity_identities(oracle_mod):
+    rng = np.random.default_rng(4)
+    n, K = 200, 8
+    X = rng.normal(size=(n, K))
+    g = W.random_sparse(n, 800, seed=5)
+    d, a = oracle_mod.affinity(n, g.u, g.v, X, want_a=True)
+    assert (a >= 0).all() and (a <= 1 + 1e-15).all()
+    assert (d >= 0).all() and (d <= 1 + 1e-15).all()
+    lo = a < 0.5
+    assert np.max(np.abs(d[lo] - (1 - a[lo]))) < 1e-15
+    assert np.max(np.abs(d - (1 - a))) < 1e-14
+    # symmetric in its two endpoints, bit for bit
+    d2 = oracle_mod.affinity(n, g.v, g.u, X)
+    assert np.array_equal(d, d2)
+    # scale invariant per row
+    d3 = oracle_mod.affinity(n, g.u, g.v, X * rng.uniform(0.5, 3.0, size=(n, 1)))
+    assert np.max(np.abs(d3 - d)) < 1e-14
+
+
+def test_affinity_path_distance_scaling(oracle_mod):
+    # Sec. 3.2.2: on a path graph d_{p,q} grows like (p - q)^2
+    n = 2000
+    g = W.path(n)
+    X = oracle_mod.smooth(n, g.u, g.v, g.w, 8, 100)
+    p = np.arange(800, 1200)
+    med = [np.median(oracle_mod.affinity(n, p, p + s, X)) for s in (1, 2, 3)]
+    assert 3.8 < med[1] / med[0] < 4.2
+    assert 8.0 < med[2] / med[0] < 9.5
+
+
+# ---------------------------------------------------------------------------
+# Aggregation (Sec. 3.2.2, reading: greedy matching in (d, edge id) order)
+# ---------------------------------------------------------------------------
+def test_aggregate_hand_examples(oracle_mod):
+    u = np.array([0, 1, 2], np.int32)
+    v = np.array([1, 2, 3], np.int32)
+    d = np.array([0.1, 0.3, 0.2])
+    # pass 1 merges {0,1} and {2,3}; pass 2 merges the two pairs through edge 1
+    agg, nc = oracle_mod.aggregate(4, u, v, d, 1, 2)
+    assert nc == 1 and list(agg) == [0, 0, 0, 0]
+    agg, nc = oracle_mod.aggregate(4, u, v, d, 2, 2)
+    assert nc == 2 and list(agg) == [0, 0, 1, 1]
+    # target 3 allows one merge: the smallest key, edge 0
+    agg, nc = oracle_mod.aggregate(4, u, v, d, 3, 2)
+    assert nc == 3 and list(agg) == [0, 0, 1, 2]
+    # equal distances: the smaller edge id wins
+    agg, nc = oracle_mod.aggregate(3, u[:2], v[:2], np.array([0.5, 0.5]), 1, 1)
+    assert list(agg) == [0, 0, 1]
+    # labels are ranks of the smallest member: {0,3} then {1,2}
+    u2 = np.array([0, 1, 1, 2], np.int32)
+    v2 = np.array([3, 2, 3, 3], np.int32)
+    agg, nc = oracle_mod.aggregate(4, u2, v2, np.array([0.1, 0.2, 0.9, 0.9]), 1, 1)
+    assert nc == 2 and list(agg) == [0, 1, 1, 0]
+
+
+def _all_graphs(n):
+    pairs = list(itertools.combinations(range(n), 2))
+    for mask in range(1 << len(pairs)):
+        es = [pairs[i] for i in range(len(pairs)) if mask >> i & 1]
+        yield es
+
+
+def test_aggregate_equals_handshake_exhaustive(oracle_mod):
+    rng = np.random.default_rng(6)
+    count = 0
+    for n in (2, 3, 4, 5):
+        for es in _all_graphs(n):
+            if not es:
+                continue
+            u = np.array([e[0] for e in es], np.int32)
+            v = np.array([e[1] for e in es], np.int32)
+            d = rng.permutation(len(es)).astype(np.float64) / len(es)
+            for passes, target in ((1, 1), (2, 1), (2, n - 1), (3, 2)):
+                agg, nc = oracle_mod.aggregate(n, u, v, d, target, passes)
+                ref, rnc = handshake_aggregate(n, u, v, d, target, passes)
+                assert nc == rnc and list(agg) == ref, (n, es, passes, target)
+                count += 1
+    assert count > 4000
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_aggregate_equals_handshake_random(oracle_mod, seed):
+    rng = np.random.default_rng(100 + seed)
+    n = int(rng.integers(20, 150))
+    g = W.random_sparse(n, 3 * n, seed=seed)
+    # coarse distance values force many exact ties, broken by edge id
+    d = np.round(rng.uniform(0, 1, size=g.m), 1)
+    for passes, target in ((1, 1), (2, n // 4), (3, 1), (2, n - 5)):
+        agg, nc = oracle_mod.aggregate(n, g.u, g.v, d, target, passes)
+        ref, rnc = handshake_aggregate(n, g.u, g.v, d, target, passes)
+        assert nc == rnc and list(agg) == ref
+
+
+def test_aggregate_matching_properties(oracle_mod):
+    g = W.random_sparse(300, 1200, seed=7)
+    rng = np.random.default_rng(8)
+    d = rng.uniform(size=g.m)
+    agg, nc = oracle_mod.aggregate(g.n, g.u, g.v, d, 1, 1)
+    sizes = np.bincount(agg, minlength=nc)
+    assert sizes.max() <= 2
+    inner = agg[g.u] == agg[g.v]
+    # every pair is joined by an edge
+    assert inner.sum() == (sizes == 2).sum()
+    # maximal: no edge joins two singletons
+    single = sizes[agg] == 1
+    assert not np.any(single[g.u] & single[g.v])
+    # greedy certificate: every unmatched edge has an end matched by a smaller
+    # (d, id) edge -- together with validity this characterises the greedy
+    # matching uniquely
+    INF = (np.inf, g.m)
+    mkey = [INF] * g.n
+    for e in np.nonzero(inner)[0]:
+        mkey[g.u[e]] = mkey[g.v[e]] = (d[e], e)
+    for f in np.nonzero(~inner)[0]:
+        assert min(mkey[g.u[f]], mkey[g.v[f]]) < (d[f], f)
+    # labels contiguous, smallest member increasing with the label
+    first = np.array([np.min(np.nonzero(agg == c)[0]) for c in range(nc)])
+    assert np.all(np.diff(first) > 0)
+
+
+def test_aggregate_passes_and_target(oracle_mod):
+    g = W.grid2d(32, 32)
+    X = oracle_mod.smooth(g.n, g.u, g.v, g.w, 8, 5)
+    d = oracle_mod.affinity(g.n, g.u, g.v, X)
+    agg1, nc1 = oracle_mod.aggregate(g.n, g.u, g.v, d, 1, 1)
+    agg2, nc2 = oracle_mod.aggregate(g.n, g.u, g.v, d, 1, 2)
+    assert np.bincount(agg1).max() <= 2 and np.bincount(agg2).max() <= 4
+    assert nc2 < nc1 < g.n
+    # pass 2 only merges whole pass-1 aggregates
+    for c in range(nc1):
+        assert len(set(agg2[agg1 == c])) == 1
+    # the target is met exactly when truncation is needed
+    agg3, nc3 = oracle_mod.aggregate(g.n, g.u, g.v, d, 600, 2)
+    assert nc3 == 600
+
+
+# ---------------------------------------------------------------------------
+# Galerkin coarsening L_R = H_G^R L_G H_R^G (Sec. 3.2.2), P 0/1 aggregation
+# ---------------------------------------------------------------------------
+def _lap_from_edges(n, u, v, w):
+    L = np.zeros((n, n))
+    for a, b, x in zip(u, v, w):
+        L[a, b] -= x
+        L[b, a] -= x
+        L[a, a] += x
+        L[b, b] += x
+    return L
+
+
+def test_galerkin_dense_bruteforce(oracle_mod):
+    g = W.random_sparse(60, 200, seed=9)
+    rng = np.random.default_rng(10)
+    agg = rng.integers(0, 17, size=g.n).astype(np.int32)
+    agg[:17] = np.arange(17)  # every label used
+    uc, vc, wc = oracle_mod.coarsen(g.n, g.u, g.v, g.w, agg, 17)
+    P = np.zeros((g.n, 17))
+    P[np.arange(g.n), agg] = 1.0
+    ref = P.T @ oracle_mod.dense_laplacian(g.n, g.u, g.v, g.w) @ P
+    Lc = _lap_from_edges(17, uc, vc, wc)
+    assert np.max(np.abs(Lc - ref)) <= 1e-13 * np.abs(ref).max()
+    # canonical, same sparsity pattern as P^T L P
+    assert np.all(uc < vc)
+    keys = uc.astype(np.int64) * 17 + vc
+    assert np.all(np.diff(keys) > 0)
+    pattern = {(a, b) for a in range(17) for b in range(a + 1, 17) if abs(ref[a, b]) > 0}
+    assert pattern == set(zip(uc.tolist(), vc.tolist()))
+
+
+def test_galerkin_invariants(oracle_mod):
+    g = W.grid2d(30, 30)
+    X = oracle_mod.smooth(g.n, g.u, g.v, g.w, 8, 5)
+    d = oracle_mod.affinity(g.n, g.u, g.v, X)
+    agg, nc = oracle_mod.aggregate(g.n, g.u, g.v, d, 225, 2)
+    uc, vc, wc = oracle_mod.coarsen(g.n, g.u, g.v, g.w, agg, nc)
+    # constant null space kept: L_c 1 = 0
+    Lc1 = oracle_mod.laplacian_apply(nc, uc, vc, wc, np.ones(nc))
+    assert np.max(np.abs(Lc1)) < 1e-12
+    # total weight = fine weight minus the weight inside aggregates
+    internal = g.w[agg[g.u] == agg[g.v]].sum()
+    assert np.isclose(wc.sum(), g.w.sum() - internal, rtol=1e-14)
+    # quadratic form of piecewise-constant vectors is preserved
+    rng = np.random.default_rng(12)
+    for _ in range(3):
+        y = rng.normal(size=nc)
+        Py = y[agg]
+        lhs = y @ oracle_mod.laplacian_apply(nc, uc, vc, wc, y)
+        rhs = Py @ oracle_mod.laplacian_apply(g.n, g.u, g.v, g.w, Py)
+        assert np.isclose(lhs, rhs, rtol=1e-12)
+
+
+def test_galerkin_hand_example(oracle_mod):
+    u = np.array([0, 1, 2], np.int32)
+    v = np.array([1, 2, 3], np.int32)
+    w = np.array([1.0, 2.0, 3.0])
+    uc, vc, wc = oracle_mod.coarsen(4, u, v, w, np.array([0, 0, 1, 1], np.int32), 2)
+    assert list(uc) == [0] and list(vc) == [1] and list(wc) == [2.0]
+    # a square 0-1-2-3-0 with aggregates {0,2} {1,3}: four crossing edges
+    u = np.array([0, 0, 1, 2], np.int32)
+    v = np.array([1, 3, 2, 3], np.int32)
+    w = np.array([1.0, 2.0, 4.0, 8.0])
+    uc, vc, wc = oracle_mod.coarsen(4, u, v, w, np.array([0, 1, 0, 1], np.int32), 2)
+    assert list(wc) == [15.0]
+
+
+# ---------------------------------------------------------------------------
+# Eigenvalue check solvers (method of the fe_tooth eigenvalue figure)
+# ---------------------------------------------------------------------------
+def test_eig_solver_closed_forms(oracle_mod):
+    g = W.grid2d(40, 30)
+    i, j = np.meshgrid(np.arange(40), np.arange(30))
+    ref = np.sort((4 * np.sin(np.pi * i / 80) ** 2 + 4 * np.sin(np.pi * j / 60) ** 2).ravel())[1:11]
+    for dense_max in (100000, 0):  # dense eigh and shift-invert eigsh
+        ev = oracle_mod.smallest_nontrivial_eigs(g.n, g.u, g.v, g.w, 10, dense_max=dense_max)
+        assert np.allclose(ev, ref, rtol=1e-9, atol=1e-12)
+    g = W.cycle(50)
+    ev = oracle_mod.smallest_nontrivial_eigs(g.n, g.u, g.v, g.w, 6)
+    ref = np.sort(4 * np.sin(np.pi * np.arange(50) / 50) ** 2)[1:7]
+    assert np.allclose(ev, ref, atol=1e-12)
+    # two components: two zeros skipped
+    u = np.concatenate([W.path(10).u, W.path(10).u + 10]).astype(np.int32)
+    v = np.concatenate([W.path(10).v, W.path(10).v + 10]).astype(np.int32)
+    ev = oracle_mod.smallest_nontrivial_eigs(20, u, v, np.ones(18), 4)
+    jj = np.arange(1, 10)
+    ref = np.sort(np.repeat(4 * np.sin(np.pi * jj / 20) ** 2, 2))[:4]
+    assert np.allclose(ev, ref, atol=1e-12)
+    # 3-D mesh: sums of three 4 sin^2 terms
+    g = W.mesh3d(5, 4, 3)
+    g.w[:] = 1.0
+    ev = oracle_mod.smallest_nontrivial_eigs(g.n, g.u, g.v, g.w, 5)
+    t = [4 * np.sin(np.pi * np.arange(k) / (2 * k)) ** 2 for k in (5, 4, 3)]
+    ref = np.sort((t[0][None, None, :] + t[1][None, :, None] + t[2][:, None, None]).ravel())[1:6]
+    assert np.allclose(ev, ref, atol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Spectral-mismatch loss and its hand-derived adjoint
+# ---------------------------------------------------------------------------
+def _small_reduction(oracle_mod, seed=13, n=60):
+    g = W.random_sparse(n, 3 * n, seed=seed)
+    X = oracle_mod.smooth(g.n, g.u, g.v, g.w, 4, 3)
+    d = oracle_mod.affinity(g.n, g.u, g.v, X)
+    agg, nc = oracle_mod.aggregate(g.n, g.u, g.v, d, max(n // 4, 2), 2)
+    uc, vc, wc = oracle_mod.coarsen(g.n, g.u, g.v, g.w, agg, nc)
+    return g, X, agg, nc, uc, vc, wc
+
+
+def _fd_check(oracle_mod, g, X, agg, nc, uc, vc, wc, S, h=1e-4):
+    L0, grad, _, _ = oracle_mod.loss(g.n, g.u, g.v, g.w, nc, uc, vc, wc, agg, X, S)
+    fd = np.empty_like(wc)
+    for e in range(len(wc)):
+        wp = wc.copy()
+        wp[e] += h
+        wm = wc.copy()
+        wm[e] -= h
+        lp = oracle_mod.loss(g.n, g.u, g.v, g.w, nc, uc, vc, wp, agg, X, S, want_grad=False)[0]
+        lm = oracle_mod.loss(g.n, g.u, g.v, g.w, nc, uc, vc, wm, agg, X, S, want_grad=False)[0]
+        fd[e] = (lp - lm) / (2 * h)
+    floor = 1e-10 * np.abs(grad).max()
+    rel = np.abs(grad - fd) / np.maximum(np.abs(fd), floor)
+    return L0, grad, fd, rel
+
+
+@pytest.mark.parametrize("S", [0, 1, 3, 5])
+def test_loss_gradient_finite_differences(oracle_mod, S):
+    g, X, agg, nc, uc, vc, wc = _small_reduction(oracle_mod)
+    L0, grad, fd, rel = _fd_check(oracle_mod, g, X, agg, nc, uc, vc, wc, S)
+    assert L0 > 0
+    assert np.all((rel <= 1e-5) | (np.abs(grad - fd) <= 1e-10 * np.abs(grad).max())), rel.max()
+
+
+def test_loss_zero_for_piecewise_constant_vectors(oracle_mod):
+    # x_k = P z_k with M-weighted mean zero: y0 = z, R_c(y0) = R_f(x), loss 0
+    g, _, agg, nc, uc, vc, wc = _small_reduction(oracle_mod, seed=21)
+    rng = np.random.default_rng(22)
+    Z = rng.normal(size=(nc, 3))
+    M = np.bincount(agg, minlength=nc).astype(float)
+    Z -= (M @ Z) / M.sum()
+    X = Z[agg]
+    L0, _, Rf, Rc = oracle_mod.loss(g.n, g.u, g.v, g.w, nc, uc, vc, wc, agg, X, 0)
+    assert np.allclose(Rc, Rf, rtol=1e-12)
+    assert L0 < 1e-24
+
+
+def test_loss_scale_invariance(oracle_mod):
+    g, X, agg, nc, uc, vc, wc = _small_reduction(oracle_mod, seed=31)
+    for S in (0, 4):
+        l1 = oracle_mod.loss(g.n, g.u, g.v, g.w, nc, uc, vc, wc, agg, X, S, want_grad=False)[0]
+        l2 = oracle_mod.loss(g.n, g.u, g.v, g.w, nc, uc, vc, wc, agg, 3.0 * X, S, want_grad=False)[0]
+        assert np.isclose(l1, l2, rtol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Level loop and stored oracle results
+# ---------------------------------------------------------------------------
+def test_multilevel_grid(oracle_mod):
+    g = W.grid2d(64, 64)
+    levels = oracle_mod.reduce_multilevel(g.n, g.u, g.v, g.w, 8, 5, final_target=64)
+    ns = [lv.n for lv in levels] + [levels[-1].nc]
+    assert ns[0] == 4096 and ns[-1] <= 64
+    assert all(b < a for a, b in zip(ns, ns[1:]))
+    comp = oracle_mod.compose_maps(levels)
+    assert comp.min() == 0 and comp.max() == levels[-1].nc - 1
+
+
+def test_golden_grid64(oracle_mod):
+    """The committed script tests/golden/make_golden.py wrote this file by
+    calling the oracle; it also guards the oracle's bit-stability across
+    machines (x86 here, Arm on the GPU host)."""
+    import hashlib
+    with open(os.path.join(GOLDEN, "grid64_oracle.json")) as f:
+        ref = json.load(f)
+    g = W.grid2d(64, 64)
+    X = oracle_mod.smooth(g.n, g.u, g.v, g.w, 8, 5, 0.7, 0, 0)
+    d = oracle_mod.affinity(g.n, g.u, g.v, X)
+    agg, nc = oracle_mod.aggregate(g.n, g.u, g.v, d, 1024, 2)
+    uc, vc, wc = oracle_mod.coarsen(g.n, g.u, g.v, g.w, agg, nc)
+    assert hashlib.sha256(X.tobytes()).hexdigest() == ref["X_sha256"]
+    assert hashlib.sha256(d.tobytes()).hexdigest() == ref["d_sha256"]
+    assert nc == ref["nc"] and len(uc) == ref["mc"]
+    assert hashlib.sha256(agg.tobytes()).hexdigest() == ref["agg_sha256"]
+    assert float(wc.sum()) == ref["wc_sum"]
