@@ -1,0 +1,383 @@
+#!/usr/bin/env python
+"""Benchmark of the Phase (A) level loop (arXiv 1812.08942, Sec. 3.2):
+smoothing -> affinity -> aggregation -> Galerkin coarsening, level by level,
+on a synthetic graph shaped like the paper's workloads.
+
+One step = graph_reduce_create (CSR of the input edge list already resident
+in HBM) + graph_reduce_multilevel (all levels down to the final target).
+Metric: input edges per second summed over levels, i.e. sum_l m_l / t_step,
+aggregated over all ranks (replicas; the path does not shard here).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload chunglu_434k|mesh3d_128|knn_200k|grid2d_64|knn_1m]
+
+Under torchrun (N > 1) every rank runs an independent replica.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "input edges/s per aggregation level (sum over levels of m_l / step time)"
+UNIT = "edges/s"
+DEFAULT_WORKLOAD = "chunglu_434k"
+# bounded oracle sample: the same Chung-Lu recipe at 1/8 scale
+SAMPLE_DIV = 8
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")), int(
+        os.environ.get("WORLD_SIZE", "1"))
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# Algorithmic bytes of one Jacobi sweep (the dominant kernel): every CSR slot
+# read once (column index + row-scaled weight), the row pointers, the vector
+# block read once and written once.
+# ---------------------------------------------------------------------------
+def sweep_bytes(n, m, K, xbytes, wbytes):
+    return 2 * m * (4 + wbytes) + 8 * (n + 1) + 2 * n * K * xbytes
+
+
+def kernel_source_sha(path):
+    import hashlib
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def traffic_from_profile(workload, src_sha):
+    """dram bytes per sweep launch from the committed ncu summary, if it was
+    taken on the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "k_sweep_%s.md" % workload)
+    if not os.path.exists(p):
+        return None
+    txt = open(p).read()
+    m_sha = re.search(r"source_sha256_16:\s*([0-9a-f]+)", txt)
+    m_tr = re.search(r"traffic_bytes_per_launch_level0:\s*([0-9.eE+]+)", txt)
+    if not m_sha or not m_tr or m_sha.group(1) != src_sha:
+        return None
+    return float(m_tr.group(1))
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# Oracle timing (CPU baseline / reference arm)
+# ---------------------------------------------------------------------------
+def oracle_sample_graph(workload):
+    import workloads as W
+    if workload == "chunglu_434k":
+        g = W.chung_lu(434_000 // SAMPLE_DIV, 16_000_000 // SAMPLE_DIV)
+        desc = "Chung-Lu recipe at 1/%d scale (%d nodes, %d edges, same mean degree and exponent)" % (
+            SAMPLE_DIV, g.n, g.m)
+    elif workload == "mesh3d_128":
+        g = W.mesh3d(64, 64, 64)
+        desc = "64^3 7-point mesh, log-normal weights (1/8 of the nodes)"
+    elif workload == "grid2d_64":
+        g = W.grid2d(64, 64)
+        desc = "the full 64x64 grid"
+    else:
+        g = W.chung_lu(434_000 // SAMPLE_DIV, 16_000_000 // SAMPLE_DIV)
+        desc = "Chung-Lu recipe at 1/%d scale" % SAMPLE_DIV
+    return g, desc
+
+
+def time_oracle_multilevel(g, wl):
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    levels = oracle.reduce_multilevel(g.n, g.u, g.v, g.w, wl.K, wl.sweeps, wl.omega,
+                                      final_target=max(1, int(wl.final_target * g.n / wl_full_n(wl))))
+    dt = time.perf_counter() - t0
+    edges = sum(lv.m for lv in levels)
+    return edges, dt, len(levels)
+
+
+def wl_full_n(wl):
+    return {"chunglu_434k": 434_000, "mesh3d_128": 2_097_152, "knn_200k": 200_000, "grid2d_64": 4096,
+            "knn_1m": 1_000_000}.get(wl.name, 434_000)
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return 0
+    import workloads as W
+    wl = W.WORKLOADS[args.workload]
+    g, desc = oracle_sample_graph(args.workload)
+    times = []
+    edges = 0
+    for i in range(args.warmup + args.steps):
+        e, dt, nl = time_oracle_multilevel(g, wl)
+        if i >= args.warmup:
+            times.append(dt)
+            edges = e
+    total = sum(times)
+    value = edges * len(times) / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "sample": desc, "K": wl.K, "sweeps": wl.sweeps, "omega": wl.omega},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "FP64 C oracle, single thread, full level loop on " + desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# Our arm
+# ---------------------------------------------------------------------------
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    rank, local_rank, world = dist_env()
+    import torch
+    import torch.distributed as dist
+
+    if world > 1:
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import numpy as np
+
+    import paper_1812_08942_gb300 as gr
+    import workloads as W
+
+    wl = W.WORKLOADS[args.workload]
+    g = wl.make(device=dev)
+    prec = {"f64": gr.GR_F64, "f32": gr.GR_F32, "bf16": gr.GR_BF16}[wl.precision]
+    xbytes = {"f64": 8, "f32": 4, "bf16": 2}[wl.precision]
+    wbytes = 8 if wl.precision == "f64" else 4
+    params = gr.ReduceParams(K=wl.K, sweeps=wl.sweeps, omega=wl.omega, seed=0, prec=prec, passes=2,
+                             level_ratio=4, final_target=wl.final_target, max_levels=32)
+    # inputs resident in HBM before the timed region
+    u_d = torch.from_numpy(g.u).to(dev)
+    v_d = torch.from_numpy(g.v).to(dev)
+    w_d = torch.from_numpy(g.w).to(dev)
+    torch.cuda.synchronize()
+
+    def step():
+        G = gr.graph_reduce_create(g.n, u_d, v_d, w_d)
+        levels, stats = gr.graph_reduce_multilevel(G, params, want_stats=True)
+        return G, levels, stats
+
+    for _ in range(args.warmup):
+        G, levels, stats = step()
+        del G, levels
+    torch.cuda.synchronize()
+
+    gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local_rank)).split(",")[0]) if world == 1 else local_rank
+    sampler = ClockSampler(gpu_index if world == 1 else local_rank)
+    sampler.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = gr.graph_reduce_launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    all_stats = []
+    for _ in range(args.steps):
+        G, levels, stats = step()
+        all_stats.append(stats)
+        del G, levels
+    ev1.record()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    launches = gr.graph_reduce_launch_count() - launches0
+    clocks = sampler.stop()
+    t_ms = ev0.elapsed_time(ev1)
+    t_max = t_ms
+    if world > 1:
+        tt = torch.tensor([t_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    edges_per_step = sum(s["m"] for s in all_stats[-1])
+    value = edges_per_step * args.steps * world / (t_max / 1000.0)
+
+    # roofline of the dominant kernel: the Jacobi sweep (bytes / event time)
+    sw_bytes = 0.0
+    sw_ms = 0.0
+    sw_launches = 0
+    for stats in all_stats:
+        for s in stats:
+            sw_bytes += s["sweeps"] * sweep_bytes(s["n"], s["m"], wl.K, xbytes, wbytes)
+            sw_ms += s["t_sweeps"]
+            sw_launches += s["sweeps"]
+    peak, peak_kind = load_peaks()
+    achieved = sw_bytes / (sw_ms / 1000.0) / 1e9 if sw_ms > 0 else 0.0
+    src_sha = kernel_source_sha(os.path.join(ROOT, "paper_1812_08942_gb300", "csrc", "gr_smooth.cu"))
+    traffic = traffic_from_profile(args.workload, src_sha)
+    lv0 = all_stats[-1][0]
+    roofline = {
+        "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+        "peak_kind": peak_kind, "kernel": "k_sweep (weighted-Jacobi multi-vector SpMM)",
+        "bytes_per_launch_level0": sweep_bytes(lv0["n"], lv0["m"], wl.K, xbytes, wbytes),
+        "traffic": traffic, "launches": sw_launches, "avg_launch_ms": sw_ms / max(sw_launches, 1),
+    }
+    per_level = []
+    for s in all_stats[-1]:
+        t = s["t_smooth"] + s["t_affinity"] + s["t_aggregate"] + s["t_coarsen"]
+        per_level.append({"n": s["n"], "m": s["m"], "nc": s["nc"], "mc": s["mc"], "rounds": s["rounds"],
+                          "t_smooth_ms": round(s["t_smooth"], 4), "t_affinity_ms": round(s["t_affinity"], 4),
+                          "t_aggregate_ms": round(s["t_aggregate"], 4), "t_coarsen_ms": round(s["t_coarsen"], 4),
+                          "edges_per_s": s["m"] / (t / 1000.0) if t > 0 else None})
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        uh = torch.from_numpy(g.u).pin_memory()
+        vh = torch.from_numpy(g.v).pin_memory()
+        wh = torch.from_numpy(g.w).pin_memory()
+        h2d = g.m * (4 + 4 + 8)
+        d2h = 0
+        k_e2e = max(1, min(args.steps, 5))
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(k_e2e):
+            G = gr.graph_reduce_create(g.n, uh, vh, wh)
+            levels, _ = gr.graph_reduce_multilevel(G, params, want_stats=False)
+            fu, fv, fw = gr.graph_reduce_get_edges(levels[-1], on_host=True)
+            comp = gr.graph_reduce_compose_maps(levels).cpu()
+            d2h = levels[-1].m * 16 + comp.numel() * 4
+            del G, levels
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        if world > 1:
+            tt = torch.tensor([te], dtype=torch.float64, device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            te = float(tt.item())
+        e2e = {"value": edges_per_step * k_e2e * world / te, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "steps": k_e2e}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        gs, desc = oracle_sample_graph(args.workload)
+        e, dt, nl = time_oracle_multilevel(gs, wl)
+        cpu = {"value": e / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "FP64 C oracle, single thread, full level loop (%d levels) on %s, %.1f s" % (nl, desc, dt)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": wl.precision, "data": "synthetic",
+            "config": {"workload": wl.name, "n": g.n, "m": g.m, "K": wl.K, "sweeps": wl.sweeps,
+                       "omega": wl.omega, "passes": 2, "level_ratio": 4, "final_target": wl.final_target,
+                       "levels": len(all_stats[-1]), "edges_per_step": edges_per_step,
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (edge list %.0f MB + CSR %.0f MB vs 129 MB); no flush"
+                             % (g.m * 16 / 1e6, g.m * 2 * 24 / 1e6)},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "clocks": clocks, "levels": per_level,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

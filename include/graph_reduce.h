@@ -1,0 +1,222 @@
+/*
+ * graph_reduce.h -- C ABI of the GB300 (sm_103a) spectral node-aggregation
+ * library: the Phase (A) hot path of "Nearly-Linear Time Spectral Graph
+ * Reduction for Scalable Graph Partitioning and Data Visualization"
+ * (Zhao, Wang, Feng; arXiv 1812.08942).
+ *
+ * The problem statement (Sec. 3.1, Table "symbol", Alg. 4): given the graph
+ * Laplacian L_G of a weighted undirected graph, produce a much smaller graph
+ * R with Laplacian L_R = H_G^R L_G H_R^G and the node mapping H between them.
+ * One level of Phase (A) is
+ *     smooth    K random test vectors by weighted-Jacobi sweeps (Alg. 3),
+ *     affinity  per-edge spectral affinity / algebraic distance (Eq. eqn:agg),
+ *     aggregate nodes joined by small algebraic distance (Sec. 3.2.2),
+ *     coarsen   Galerkin product L_R = P^T L_G P (Sec. 3.2.2),
+ * repeated level by level.
+ *
+ * Conventions for every call
+ *   Graph input  canonical undirected edge list: u[e] < v[e] < n, sorted by
+ *                (u, v), no duplicates, w[e] finite and > 0.  The edge id of an
+ *                edge is its position e in that list; every per-edge array
+ *                (d, a, w_c, gradients) is indexed by it.
+ *   Pointers     device pointers on the context's stream unless the argument
+ *                name or a flag says host.  Vector blocks are row-major n x K
+ *                (entry (i, k) at X[i*K + k]).
+ *   Ownership    the caller owns every buffer it passes; a context owns the
+ *                device copy of its graph and its scratch, all released by
+ *                graph_reduce_destroy.  Contexts returned by coarsen /
+ *                multilevel are owned by the caller and destroyed separately.
+ *   Ordering     work is enqueued on the context's CUDA stream; calls that
+ *                return a host value (counts, sizes) synchronise that stream.
+ *                One context is used by one host thread at a time.
+ *   Errors       no exception crosses the ABI.  On a non-zero status the
+ *                outputs are unspecified and graph_reduce_last_error(ctx)
+ *                describes the failure; the context stays usable except after
+ *                GR_ECUDA caused by a sticky CUDA error.
+ */
+#ifndef GRAPH_REDUCE_H
+#define GRAPH_REDUCE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gr_ctx gr_ctx;
+
+typedef enum {
+    GR_OK = 0,
+    GR_EINVAL = 1,    /* invalid argument or non-canonical graph            */
+    GR_ENOMEM = 2,    /* device allocation failed                           */
+    GR_ECUDA = 3,     /* CUDA runtime error                                 */
+    GR_ETIMEOUT = 4,  /* aggregation exceeded its handshake round limit     */
+    GR_ESTATE = 5     /* call not valid for this context                    */
+} gr_status;
+
+/* Arithmetic of the test-vector block.  GR_F64: FP64 storage and arithmetic.
+ * GR_F32: FP32 storage and accumulation, FP64 column statistics.  GR_BF16:
+ * BF16 storage of X, FP32 accumulation, FP64 column statistics. */
+typedef enum { GR_F64 = 0, GR_F32 = 1, GR_BF16 = 2 } gr_prec;
+
+/* Build a context: the symmetric CSR of the adjacency A_G, the weighted
+ * degrees D_G(i,i) = sum_j w_ij (ascending edge id) and the row-scaled weights
+ * w_ij / D_G(i,i) used by D_G^-1 A_G (Sec. 2.1, Laplacian definition; Alg. 3).
+ *   n, m             node and edge count (n >= 1, 0 <= m < 2^31)
+ *   u, v, w          canonical edge list, host arrays if inputs_on_host else
+ *                    device arrays; copied, not retained
+ *   cuda_stream      cudaStream_t for all work of this context (NULL: legacy
+ *                    default stream)
+ * GR_EINVAL if the list is not canonical (checked on every create). */
+gr_status graph_reduce_create(gr_ctx** out, int64_t n, int64_t m, const int32_t* u,
+                              const int32_t* v, const double* w, int inputs_on_host,
+                              void* cuda_stream);
+
+/* Node and edge count of a context (host outputs, either may be NULL). */
+gr_status graph_reduce_get_info(const gr_ctx* ctx, int64_t* n_out, int64_t* m_out);
+
+/* Test-vector smoothing (Sec. 3.2.1 with the weighted-Jacobi relaxation of
+ * Alg. 3).  Draws X0 (n x K, entry (i,k) = 2u - 1 with u the top 53 bits of
+ * output number c+1 of SplitMix64 seeded with `seed`, c = level*2^40 + i*K +
+ * k), centres every column (1^T x = 0) and scales it to unit 2-norm, then runs
+ * `sweeps` sweeps x <- (1-omega) x + omega D^-1 A x, each followed by the same
+ * centring and normalisation (column statistics in FP64).  An isolated node
+ * keeps its value in a sweep.
+ *   K        number of test vectors: 4, 8, 16, 24 or 32
+ *   prec     GR_F64 / GR_F32 / GR_BF16: X is double / float / bfloat16
+ *   X        device output, n x K row-major */
+gr_status graph_reduce_smooth(gr_ctx* ctx, int K, int sweeps, double omega, uint64_t seed,
+                              int level, gr_prec prec, void* X);
+
+/* Per-edge affinity a = (X_p,X_q)^2 / ((X_p,X_p)(X_q,X_q)) (Eq. eqn:agg) and
+ * algebraic distance d = 1 - a (Sec. 3.2.2), for every edge (p, q) of the
+ * canonical list.  d is evaluated without cancellation as
+ * |h_p - h_q|^2 |h_p + h_q|^2 / 4 with h = X_row / |X_row|; a zero row gives
+ * a = 0, d = 1.
+ *   X        device, n x K in the storage type of prec
+ *   d_out    device, m entries: double for GR_F64, float otherwise
+ *   a_out    device, m entries of the same type, or NULL */
+gr_status graph_reduce_affinity(gr_ctx* ctx, const void* X, int K, gr_prec prec, void* d_out,
+                                void* a_out);
+
+/* Node aggregation by algebraic distance (Sec. 3.2.2).  The paper names no
+ * scheme; this one is greedy matching in ascending (d, edge id) order, run in
+ * `passes` passes on the cluster graph (the key of a cluster pair is its
+ * smallest fine (d, id)), each pass making at most n_cur - target_nc merges and
+ * passes stopping once n_cur <= target_nc.  Computed by rounds of a lock-free
+ * handshake (mutual best neighbours merge), which yields exactly the greedy
+ * matching.  Coarse label = rank of the aggregate's smallest fine node.
+ *   d            device, m distances (double if d_is_f64 else float), >= 0
+ *   target_nc    >= 1
+ *   max_rounds   handshake rounds allowed per pass (<= 0: n + 64)
+ *   agg_out      device, n labels in [0, nc)
+ *   nc_out       host, number of aggregates
+ *   rounds_out   host, total handshake rounds, or NULL
+ * GR_ETIMEOUT if a pass needs more than max_rounds rounds. */
+gr_status graph_reduce_aggregate(gr_ctx* ctx, const void* d, int d_is_f64, int64_t target_nc,
+                                 int passes, int max_rounds, int32_t* agg_out, int64_t* nc_out,
+                                 int32_t* rounds_out);
+
+/* Galerkin reduced graph L_R = H_G^R L_G H_R^G (Sec. 3.2.2) with H_R^G = P,
+ * P[i, agg[i]] = 1, H_G^R = P^T: one reduced edge (A < B) per pair of
+ * aggregates joined by fine edges, its weight the FP64 sum of those fine
+ * weights in ascending fine edge id; edges inside an aggregate vanish.
+ * Returns a new context on the same stream that also keeps `agg` as its
+ * mapping from the parent level.
+ *   agg      device, n labels in [0, nc); every label must be used */
+gr_status graph_reduce_coarsen(gr_ctx* ctx, const int32_t* agg, int64_t nc, gr_ctx** coarse_out);
+
+/* Copy the canonical edge list out.  Pass NULL for u, v and w to query the
+ * count only.  outputs_on_host selects host or device destinations. */
+gr_status graph_reduce_get_edges(const gr_ctx* ctx, int64_t* m_out, int32_t* u, int32_t* v,
+                                 double* w, int outputs_on_host);
+
+/* Copy the mapping a coarse context was built with (parent node -> this
+ * context's node), n_parent entries, to device memory `agg_out`.
+ * GR_ESTATE for a context not made by coarsen. */
+gr_status graph_reduce_get_map(const gr_ctx* ctx, int32_t* agg_out, int64_t* n_parent_out);
+
+/* Parameters of the level loop. */
+typedef struct gr_params {
+    int K;                 /* test vectors per level                          */
+    int sweeps;            /* Jacobi sweeps per level                         */
+    double omega;          /* Jacobi weight (theta of Alg. 3)                 */
+    uint64_t seed;         /* test-vector seed; level l uses counter block l  */
+    int prec;              /* gr_prec of X                                    */
+    int passes;            /* aggregation passes per level                    */
+    int level_ratio;       /* level target = max(ceil(n/level_ratio), final)  */
+    int64_t final_target;  /* stop once n <= final_target                     */
+    int max_levels;        /* capacity of levels_out                          */
+    int max_rounds;        /* handshake round limit per pass (<= 0: default)  */
+} gr_params;
+
+/* Per-level record filled by graph_reduce_multilevel (host).  Times are CUDA
+ * event intervals on the context stream, in milliseconds; t_sweeps covers
+ * only the `sweeps` Jacobi sweep kernels inside t_smooth. */
+typedef struct gr_level_stats {
+    int64_t n, m, nc, mc;
+    int32_t rounds;
+    int32_t sweeps;
+    float t_smooth, t_affinity, t_aggregate, t_coarsen;
+    float t_sweeps;
+} gr_level_stats;
+
+/* The level loop of Phase (A): on level l (fine context = level 0) run
+ * smooth(seed, level l) -> affinity -> aggregate(target max(ceil(n_l /
+ * level_ratio), final_target)) -> coarsen, until n_l <= final_target, a level
+ * makes no merge, or max_levels levels exist.
+ *   levels_out   host array of max_levels; receives the coarse contexts
+ *                (owned by the caller) in order
+ *   nlevels_out  host, number of coarse contexts produced
+ *   stats_out    host array of max_levels records, or NULL */
+gr_status graph_reduce_multilevel(gr_ctx* fine, const gr_params* params, gr_ctx** levels_out,
+                                  int* nlevels_out, gr_level_stats* stats_out);
+
+/* Compose the maps of a chain of coarse contexts (levels[0] made from the
+ * fine graph, levels[i] from levels[i-1]) into one fine -> coarsest map.
+ *   agg_out  device, n_fine entries */
+gr_status graph_reduce_compose_maps(gr_ctx* const* levels, int nlevels, int32_t* agg_out);
+
+/* Spectral-mismatch loss on a reduced graph with free edge weights w_c (not
+ * in the paper; it makes the edge-weight sensitivity of Sec. 3.3.3 an exact
+ * gradient).  With x_k the columns of X on the fine graph, P the map `agg`
+ * (fine -> coarse context nodes) and M_A = |{i : agg[i] = A}|:
+ *   R_f[k] = x_k^T L_G x_k / x_k^T x_k
+ *   y_0    = M^-1 P^T X                      (aggregate means)
+ *   y_{s+1} = (1-omega) y_s + omega D_c^-1 A_c y_s,  s < sweeps_c,
+ *            where A_c, D_c use the weights w_c on the coarse edge list
+ *   R_c[k] = y^T L_c y / sum_A M_A (y_A - mu_k)^2,  mu_k = sum M_A y_A / sum M
+ *   loss   = (1/K) sum_k (R_c[k] / R_f[k] - 1)^2
+ *   X        device float, fine n x K;  w_c  device float, coarse m entries
+ *   loss_out device float scalar
+ *   saved    device float, coarse_n*(K+1) + K entries: receives y_0, R_f and M
+ *            for graph_reduce_loss_bwd (nothing else is kept)
+ * K: 4, 8, 16, 24 or 32. */
+gr_status graph_reduce_loss_fwd(gr_ctx* fine, gr_ctx* coarse, const int32_t* agg, const float* X,
+                                int K, const float* w_c, int sweeps_c, double omega,
+                                float* loss_out, float* saved);
+
+/* Adjoint of graph_reduce_loss_fwd with respect to w_c: recomputes the
+ * sweeps from the saved y_0, then runs the reverse sweeps.
+ *   grad_loss   device float scalar (upstream gradient)
+ *   grad_w_out  device float, coarse m entries (overwritten) */
+gr_status graph_reduce_loss_bwd(gr_ctx* coarse, const float* saved, int K, const float* w_c,
+                                int sweeps_c, double omega, const float* grad_loss,
+                                float* grad_w_out);
+
+/* Number of kernels this library has launched in the process so far (a
+ * diagnostic counter, not tied to any paper passage). */
+uint64_t graph_reduce_launch_count(void);
+
+/* Text of the last error on ctx (or of the last failed create when ctx is
+ * NULL).  Valid until the next call on the same context. */
+const char* graph_reduce_last_error(const gr_ctx* ctx);
+
+/* Release a context and everything it owns.  NULL-safe. */
+void graph_reduce_destroy(gr_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GRAPH_REDUCE_H */

@@ -1,0 +1,304 @@
+"""ctypes binding of libgraphreduce (include/graph_reduce.h).
+
+Argument marshalling only: every function here forwards torch tensors (device
+memory, current CUDA stream) to the C entry point of the same name.  There is
+no CPU fallback; if the library is missing, loading it raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libgraphreduce.so")
+_lib = None
+
+GR_OK, GR_EINVAL, GR_ENOMEM, GR_ECUDA, GR_ETIMEOUT, GR_ESTATE = range(6)
+GR_F64, GR_F32, GR_BF16 = 0, 1, 2
+_STATUS = {1: "GR_EINVAL", 2: "GR_ENOMEM", 3: "GR_ECUDA", 4: "GR_ETIMEOUT", 5: "GR_ESTATE"}
+
+EXPORTED = [
+    "graph_reduce_create", "graph_reduce_get_info", "graph_reduce_smooth", "graph_reduce_affinity",
+    "graph_reduce_aggregate", "graph_reduce_coarsen", "graph_reduce_get_edges", "graph_reduce_get_map",
+    "graph_reduce_multilevel", "graph_reduce_compose_maps", "graph_reduce_loss_fwd",
+    "graph_reduce_loss_bwd", "graph_reduce_launch_count", "graph_reduce_last_error", "graph_reduce_destroy",
+]
+
+
+class GraphReduceError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (_STATUS.get(status, str(status)), msg))
+        self.status = status
+
+
+class gr_params(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int), ("sweeps", ctypes.c_int), ("omega", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("prec", ctypes.c_int), ("passes", ctypes.c_int),
+                ("level_ratio", ctypes.c_int), ("final_target", ctypes.c_int64),
+                ("max_levels", ctypes.c_int), ("max_rounds", ctypes.c_int)]
+
+
+class gr_level_stats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("m", ctypes.c_int64), ("nc", ctypes.c_int64), ("mc", ctypes.c_int64),
+                ("rounds", ctypes.c_int32), ("sweeps", ctypes.c_int32), ("t_smooth", ctypes.c_float),
+                ("t_affinity", ctypes.c_float), ("t_aggregate", ctypes.c_float), ("t_coarsen", ctypes.c_float),
+                ("t_sweeps", ctypes.c_float)]
+
+
+def lib_path() -> str:
+    return _LIB_PATH
+
+
+def load():
+    """Load libgraphreduce.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError("libgraphreduce.so is not built; run python -m paper_1812_08942_gb300.build")
+    lib = ctypes.CDLL(_LIB_PATH)
+    P, I, I64, D, U64, I32 = (ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double,
+                              ctypes.c_uint64, ctypes.c_int32)
+    PP = ctypes.POINTER(ctypes.c_void_p)
+    sig = {
+        "graph_reduce_create": (I, [PP, I64, I64, P, P, P, I, P]),
+        "graph_reduce_get_info": (I, [P, ctypes.POINTER(I64), ctypes.POINTER(I64)]),
+        "graph_reduce_smooth": (I, [P, I, I, D, U64, I, I, P]),
+        "graph_reduce_affinity": (I, [P, P, I, I, P, P]),
+        "graph_reduce_aggregate": (I, [P, P, I, I64, I, I, P, ctypes.POINTER(I64), ctypes.POINTER(I32)]),
+        "graph_reduce_coarsen": (I, [P, P, I64, PP]),
+        "graph_reduce_get_edges": (I, [P, ctypes.POINTER(I64), P, P, P, I]),
+        "graph_reduce_get_map": (I, [P, P, ctypes.POINTER(I64)]),
+        "graph_reduce_multilevel": (I, [P, ctypes.POINTER(gr_params), PP, ctypes.POINTER(I),
+                                        ctypes.POINTER(gr_level_stats)]),
+        "graph_reduce_compose_maps": (I, [PP, I, P]),
+        "graph_reduce_loss_fwd": (I, [P, P, P, P, I, P, I, D, P, P]),
+        "graph_reduce_loss_bwd": (I, [P, P, I, P, I, D, P, P]),
+        "graph_reduce_launch_count": (ctypes.c_uint64, []),
+        "graph_reduce_last_error": (ctypes.c_char_p, [P]),
+        "graph_reduce_destroy": (None, [P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(st, ctx_handle):
+    if st != GR_OK:
+        msg = load().graph_reduce_last_error(ctx_handle)
+        raise GraphReduceError(st, msg.decode() if msg else "")
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(device=None):
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _prec_of(dtype):
+    if dtype == torch.float64:
+        return GR_F64
+    if dtype == torch.float32:
+        return GR_F32
+    if dtype == torch.bfloat16:
+        return GR_BF16
+    raise TypeError("X must be float64, float32 or bfloat16")
+
+
+class Graph:
+    """Owns a gr_ctx handle; destroyed with the object."""
+
+    def __init__(self, handle, n, m, device):
+        self.handle = ctypes.c_void_p(handle)
+        self.n = int(n)
+        self.m = int(m)
+        self.device = device
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.graph_reduce_destroy(h)
+            self.handle = None
+
+    def close(self):
+        self.__del__()
+
+
+# ---------------------------------------------------------------------------
+# Entry points, same names as the C ABI
+# ---------------------------------------------------------------------------
+def graph_reduce_create(n, u, v, w, device=None) -> Graph:
+    """u, v int32 and w float64, canonical.  Host tensors (or numpy arrays) are
+    copied to the device by the library; CUDA tensors are read in place."""
+    lib = load()
+    import numpy as np
+    if isinstance(u, np.ndarray):
+        u, v, w = torch.from_numpy(np.ascontiguousarray(u, np.int32)), torch.from_numpy(
+            np.ascontiguousarray(v, np.int32)), torch.from_numpy(np.ascontiguousarray(w, np.float64))
+    on_host = not u.is_cuda
+    if on_host:
+        u, v, w = u.contiguous(), v.contiguous(), w.contiguous()
+        dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    else:
+        dev = u.device
+    assert u.dtype == torch.int32 and v.dtype == torch.int32 and w.dtype == torch.float64
+    h = ctypes.c_void_p()
+    with torch.cuda.device(dev):
+        st = lib.graph_reduce_create(ctypes.byref(h), int(n), int(u.numel()), _ptr(u), _ptr(v), _ptr(w),
+                                     1 if on_host else 0, _stream(dev))
+    _check(st, None)
+    return Graph(h.value, n, u.numel(), dev)
+
+
+def graph_reduce_smooth(g: Graph, X, sweeps, omega=0.7, seed=0, level=0):
+    """Fill X (n x K, float64 / float32 / bfloat16 on the device)."""
+    assert X.is_cuda and X.is_contiguous() and X.dim() == 2 and X.shape[0] == g.n
+    st = load().graph_reduce_smooth(g.handle, int(X.shape[1]), int(sweeps), float(omega), int(seed), int(level),
+                                    _prec_of(X.dtype), _ptr(X))
+    _check(st, g.handle)
+    return X
+
+
+def graph_reduce_affinity(g: Graph, X, d_out, a_out=None):
+    assert X.is_cuda and X.is_contiguous() and d_out.is_cuda and d_out.numel() == g.m
+    st = load().graph_reduce_affinity(g.handle, _ptr(X), int(X.shape[1]), _prec_of(X.dtype), _ptr(d_out),
+                                      _ptr(a_out))
+    _check(st, g.handle)
+    return d_out
+
+
+def graph_reduce_aggregate(g: Graph, d, target_nc, passes=2, max_rounds=0, agg_out=None):
+    """Returns (agg, nc, rounds)."""
+    assert d.is_cuda and d.numel() == g.m and d.dtype in (torch.float32, torch.float64)
+    if agg_out is None:
+        agg_out = torch.empty(g.n, dtype=torch.int32, device=d.device)
+    nc = ctypes.c_int64(0)
+    rounds = ctypes.c_int32(0)
+    st = load().graph_reduce_aggregate(g.handle, _ptr(d), 1 if d.dtype == torch.float64 else 0, int(target_nc),
+                                       int(passes), int(max_rounds), _ptr(agg_out), ctypes.byref(nc),
+                                       ctypes.byref(rounds))
+    _check(st, g.handle)
+    return agg_out, int(nc.value), int(rounds.value)
+
+
+def graph_reduce_coarsen(g: Graph, agg, nc) -> Graph:
+    assert agg.is_cuda and agg.dtype == torch.int32 and agg.numel() == g.n
+    h = ctypes.c_void_p()
+    st = load().graph_reduce_coarsen(g.handle, _ptr(agg), int(nc), ctypes.byref(h))
+    _check(st, g.handle)
+    n = ctypes.c_int64()
+    m = ctypes.c_int64()
+    load().graph_reduce_get_info(h, ctypes.byref(n), ctypes.byref(m))
+    return Graph(h.value, n.value, m.value, g.device)
+
+
+def graph_reduce_get_edges(g: Graph, on_host=False):
+    """Canonical edge list (u, v, w) as tensors (device unless on_host)."""
+    dev = torch.device("cpu") if on_host else g.device
+    kw = {"pin_memory": True} if on_host else {}
+    u = torch.empty(g.m, dtype=torch.int32, device=dev, **kw)
+    v = torch.empty(g.m, dtype=torch.int32, device=dev, **kw)
+    w = torch.empty(g.m, dtype=torch.float64, device=dev, **kw)
+    m = ctypes.c_int64()
+    st = load().graph_reduce_get_edges(g.handle, ctypes.byref(m), _ptr(u), _ptr(v), _ptr(w), 1 if on_host else 0)
+    _check(st, g.handle)
+    return u, v, w
+
+
+def graph_reduce_get_map(g: Graph):
+    n = ctypes.c_int64()
+    st = load().graph_reduce_get_map(g.handle, None, ctypes.byref(n))
+    _check(st, g.handle)
+    out = torch.empty(n.value, dtype=torch.int32, device=g.device)
+    st = load().graph_reduce_get_map(g.handle, _ptr(out), ctypes.byref(n))
+    _check(st, g.handle)
+    return out
+
+
+@dataclass
+class ReduceParams:
+    K: int = 16
+    sweeps: int = 5
+    omega: float = 0.7
+    seed: int = 0
+    prec: int = GR_F32
+    passes: int = 2
+    level_ratio: int = 4
+    final_target: int = 1
+    max_levels: int = 32
+    max_rounds: int = 0
+
+    def to_c(self):
+        return gr_params(self.K, self.sweeps, self.omega, self.seed, self.prec, self.passes, self.level_ratio,
+                         self.final_target, self.max_levels, self.max_rounds)
+
+
+def graph_reduce_multilevel(g: Graph, params: ReduceParams, want_stats=True):
+    """Returns (levels, stats): coarse Graphs in order, per-level dicts."""
+    p = params.to_c()
+    arr = (ctypes.c_void_p * params.max_levels)()
+    nl = ctypes.c_int(0)
+    stats = (gr_level_stats * params.max_levels)() if want_stats else None
+    st = load().graph_reduce_multilevel(g.handle, ctypes.byref(p), arr, ctypes.byref(nl), stats)
+    levels = []
+    for i in range(nl.value):
+        n = ctypes.c_int64()
+        m = ctypes.c_int64()
+        load().graph_reduce_get_info(arr[i], ctypes.byref(n), ctypes.byref(m))
+        levels.append(Graph(arr[i], n.value, m.value, g.device))
+    _check(st, g.handle)
+    out = []
+    if want_stats:
+        for i in range(nl.value):
+            s = stats[i]
+            out.append(dict(n=s.n, m=s.m, nc=s.nc, mc=s.mc, rounds=s.rounds, sweeps=s.sweeps, t_smooth=s.t_smooth,
+                            t_affinity=s.t_affinity, t_aggregate=s.t_aggregate, t_coarsen=s.t_coarsen,
+                            t_sweeps=s.t_sweeps))
+    return levels, out
+
+
+def graph_reduce_compose_maps(levels):
+    arr = (ctypes.c_void_p * len(levels))(*[lv.handle.value for lv in levels])
+    n = ctypes.c_int64()
+    load().graph_reduce_get_map(levels[0].handle, None, ctypes.byref(n))
+    out = torch.empty(n.value, dtype=torch.int32, device=levels[0].device)
+    st = load().graph_reduce_compose_maps(arr, len(levels), _ptr(out))
+    _check(st, levels[0].handle)
+    return out
+
+
+def graph_reduce_launch_count() -> int:
+    return int(load().graph_reduce_launch_count())
+
+
+def loss_saved_numel(nc, K):
+    return nc * (K + 1) + K
+
+
+def graph_reduce_loss_fwd(fine: Graph, coarse: Graph, agg, X, w_c, sweeps_c, omega=0.7, saved=None):
+    """Returns (loss tensor (1,), saved buffer)."""
+    K = int(X.shape[1])
+    assert X.dtype == torch.float32 and w_c.dtype == torch.float32 and w_c.numel() == coarse.m
+    loss = torch.empty(1, dtype=torch.float32, device=X.device)
+    if saved is None:
+        saved = torch.empty(loss_saved_numel(coarse.n, K), dtype=torch.float32, device=X.device)
+    st = load().graph_reduce_loss_fwd(fine.handle, coarse.handle, _ptr(agg), _ptr(X), K, _ptr(w_c), int(sweeps_c),
+                                      float(omega), _ptr(loss), _ptr(saved))
+    _check(st, fine.handle)
+    return loss, saved
+
+
+def graph_reduce_loss_bwd(coarse: Graph, saved, K, w_c, sweeps_c, omega, grad_loss, grad_w=None):
+    if grad_w is None:
+        grad_w = torch.empty(coarse.m, dtype=torch.float32, device=w_c.device)
+    st = load().graph_reduce_loss_bwd(coarse.handle, _ptr(saved), int(K), _ptr(w_c), int(sweeps_c), float(omega),
+                                      _ptr(grad_loss), _ptr(grad_w))
+    _check(st, coarse.handle)
+    return grad_w

@@ -1,0 +1,329 @@
+// The C ABI (include/graph_reduce.h): argument checks, context lifetime, the
+// level loop.  No exception crosses this boundary.
+#include <math.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+
+#include "gr_internal.cuh"
+
+namespace gr {
+
+static thread_local std::string g_create_error;
+
+gr_status set_error(gr_ctx* c, gr_status st, const std::string& msg) {
+    if (c) c->last_error = msg;
+    else g_create_error = msg;
+    return st;
+}
+
+gr_status cuda_error(gr_ctx* c, cudaError_t e, const char* where) {
+    std::string msg = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    gr_status st = (e == cudaErrorMemoryAllocation) ? GR_ENOMEM : GR_ECUDA;
+    return set_error(c, st, msg);
+}
+
+gr_status compose_impl(gr_ctx* const* levels, int nlevels, int32_t* out);
+
+static bool valid_K(int K) { return K == 4 || K == 8 || K == 16 || K == 24 || K == 32; }
+
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// canonical-list check on the host
+static bool host_canonical(int64_t n, int64_t m, const int32_t* u, const int32_t* v, const double* w,
+                           std::string* why) {
+    for (int64_t e = 0; e < m; ++e) {
+        if (u[e] < 0 || v[e] >= n || !(u[e] < v[e])) {
+            *why = "edge " + std::to_string(e) + " is not 0 <= u < v < n";
+            return false;
+        }
+        if (e > 0 && (u[e] < u[e - 1] || (u[e] == u[e - 1] && v[e] <= v[e - 1]))) {
+            *why = "edge " + std::to_string(e) + " breaks the sorted, duplicate-free order";
+            return false;
+        }
+        if (!(w[e] > 0.0) || !isfinite(w[e])) {
+            *why = "edge " + std::to_string(e) + " has a weight that is not finite and > 0";
+            return false;
+        }
+    }
+    return true;
+}
+
+__global__ void k_canonical_check(int64_t n, int64_t m, const int32_t* __restrict__ u,
+                                  const int32_t* __restrict__ v, const double* __restrict__ w,
+                                  int32_t* __restrict__ bad) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m) return;
+    int32_t a = u[e], b = v[e];
+    bool ok = a >= 0 && b < n && a < b && w[e] > 0.0 && isfinite(w[e]);
+    if (e > 0) {
+        int32_t pa = u[e - 1], pb = v[e - 1];
+        ok = ok && (pa < a || (pa == a && pb < b));
+    }
+    if (!ok) atomicExch(bad, 1);
+}
+
+}  // namespace gr
+
+using namespace gr;
+
+extern "C" {
+
+gr_status graph_reduce_create(gr_ctx** out, int64_t n, int64_t m, const int32_t* u, const int32_t* v,
+                              const double* w, int inputs_on_host, void* cuda_stream) {
+    if (!out) return set_error(nullptr, GR_EINVAL, "create: out is NULL");
+    *out = nullptr;
+    if (n < 1 || n >= (1ll << 31)) return set_error(nullptr, GR_EINVAL, "create: n must be in [1, 2^31)");
+    if (m < 0 || m >= (1ll << 31)) return set_error(nullptr, GR_EINVAL, "create: m must be in [0, 2^31)");
+    if (m > 0 && (!u || !v || !w)) return set_error(nullptr, GR_EINVAL, "create: edge arrays are NULL");
+    if (inputs_on_host && m > 0) {
+        std::string why;
+        if (!host_canonical(n, m, u, v, w, &why)) return set_error(nullptr, GR_EINVAL, "create: " + why);
+    }
+    gr_ctx* c = new (std::nothrow) gr_ctx();
+    if (!c) return set_error(nullptr, GR_ENOMEM, "create: host allocation failed");
+    c->n = n;
+    c->m = m;
+    c->stream = (cudaStream_t)cuda_stream;
+    c->ws.stream = c->stream;
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (e == cudaSuccess) tune_mempool(c->device);
+    int64_t* hs = host_scratch();
+    if (e == cudaSuccess && !hs) e = cudaErrorMemoryAllocation;
+    size_t me = (size_t)(m > 0 ? m : 1);
+    if (e == cudaSuccess) e = cudaMallocAsync(&c->eu, sizeof(int32_t) * me, c->stream);
+    if (e == cudaSuccess) e = cudaMallocAsync(&c->ev, sizeof(int32_t) * me, c->stream);
+    if (e == cudaSuccess) e = cudaMallocAsync(&c->ew, sizeof(double) * me, c->stream);
+    cudaMemcpyKind kind = inputs_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    if (e == cudaSuccess && m > 0) e = cudaMemcpyAsync(c->eu, u, sizeof(int32_t) * m, kind, c->stream);
+    if (e == cudaSuccess && m > 0) e = cudaMemcpyAsync(c->ev, v, sizeof(int32_t) * m, kind, c->stream);
+    if (e == cudaSuccess && m > 0) e = cudaMemcpyAsync(c->ew, w, sizeof(double) * m, kind, c->stream);
+    if (e != cudaSuccess) {
+        cuda_error(nullptr, e, "create");
+        graph_reduce_destroy(c);
+        return e == cudaErrorMemoryAllocation ? GR_ENOMEM : GR_ECUDA;
+    }
+    if (!inputs_on_host && m > 0) {
+        int32_t* bad = (int32_t*)(hs + 4);
+        *bad = 0;
+        void* dbad;
+        e = c->ws.get(WS_COARSE_TMP, 16, &dbad);
+        if (e == cudaSuccess) e = cudaMemsetAsync(dbad, 0, 4, c->stream);
+        if (e == cudaSuccess) {
+            k_canonical_check<<<(unsigned)ceil_div(m, 256), 256, 0, c->stream>>>(n, m, c->eu, c->ev, c->ew,
+                                                                                (int32_t*)dbad); count_launch();
+            e = cudaMemcpyAsync(bad, dbad, 4, cudaMemcpyDeviceToHost, c->stream);
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess || *bad) {
+            if (e != cudaSuccess) cuda_error(nullptr, e, "create");
+            else set_error(nullptr, GR_EINVAL, "create: the edge list is not canonical (u < v < n, sorted, unique, w > 0 finite)");
+            graph_reduce_destroy(c);
+            return e != cudaSuccess ? GR_ECUDA : GR_EINVAL;
+        }
+    }
+    gr_status st = build_csr(c);
+    if (st != GR_OK) {
+        set_error(nullptr, st, c->last_error);
+        graph_reduce_destroy(c);
+        return st;
+    }
+    *out = c;
+    return GR_OK;
+}
+
+gr_status graph_reduce_get_info(const gr_ctx* ctx, int64_t* n_out, int64_t* m_out) {
+    if (!ctx) return GR_EINVAL;
+    if (n_out) *n_out = ctx->n;
+    if (m_out) *m_out = ctx->m;
+    return GR_OK;
+}
+
+gr_status graph_reduce_smooth(gr_ctx* ctx, int K, int sweeps, double omega, uint64_t seed, int level,
+                              gr_prec prec, void* X) {
+    if (!ctx) return set_error(nullptr, GR_EINVAL, "smooth: ctx is NULL");
+    if (!valid_K(K)) return set_error(ctx, GR_EINVAL, "smooth: K must be 4, 8, 16, 24 or 32");
+    if (sweeps < 0 || !(omega > 0.0 && omega <= 1.0))
+        return set_error(ctx, GR_EINVAL, "smooth: need sweeps >= 0 and 0 < omega <= 1");
+    if (level < 0 || level >= (1 << 20)) return set_error(ctx, GR_EINVAL, "smooth: level out of range");
+    if (!X || !aligned16(X)) return set_error(ctx, GR_EINVAL, "smooth: X must be a 16-byte aligned device pointer");
+    if (prec != GR_F64 && prec != GR_F32 && prec != GR_BF16) return set_error(ctx, GR_EINVAL, "smooth: bad precision");
+    return smooth_impl(ctx, K, sweeps, omega, seed, level, prec, X);
+}
+
+gr_status graph_reduce_affinity(gr_ctx* ctx, const void* X, int K, gr_prec prec, void* d_out, void* a_out) {
+    if (!ctx) return set_error(nullptr, GR_EINVAL, "affinity: ctx is NULL");
+    if (!valid_K(K)) return set_error(ctx, GR_EINVAL, "affinity: K must be 4, 8, 16, 24 or 32");
+    if (!X || !aligned16(X) || !d_out) return set_error(ctx, GR_EINVAL, "affinity: X (16-byte aligned) and d_out required");
+    if (prec != GR_F64 && prec != GR_F32 && prec != GR_BF16) return set_error(ctx, GR_EINVAL, "affinity: bad precision");
+    return affinity_impl(ctx, X, K, prec, d_out, a_out);
+}
+
+gr_status graph_reduce_aggregate(gr_ctx* ctx, const void* d, int d_is_f64, int64_t target_nc, int passes,
+                                 int max_rounds, int32_t* agg_out, int64_t* nc_out, int32_t* rounds_out) {
+    if (!ctx) return set_error(nullptr, GR_EINVAL, "aggregate: ctx is NULL");
+    if (!agg_out || !nc_out || (ctx->m > 0 && !d)) return set_error(ctx, GR_EINVAL, "aggregate: NULL argument");
+    if (target_nc < 1 || passes < 0 || passes > 30)
+        return set_error(ctx, GR_EINVAL, "aggregate: need target_nc >= 1 and 0 <= passes <= 30");
+    if (rounds_out) *rounds_out = 0;
+    return aggregate_impl(ctx, d, d_is_f64, target_nc, passes, max_rounds, agg_out, nc_out, rounds_out);
+}
+
+gr_status graph_reduce_coarsen(gr_ctx* ctx, const int32_t* agg, int64_t nc, gr_ctx** coarse_out) {
+    if (!ctx) return set_error(nullptr, GR_EINVAL, "coarsen: ctx is NULL");
+    if (!agg || !coarse_out) return set_error(ctx, GR_EINVAL, "coarsen: NULL argument");
+    *coarse_out = nullptr;
+    return coarsen_impl(ctx, agg, nc, coarse_out);
+}
+
+gr_status graph_reduce_get_edges(const gr_ctx* cctx, int64_t* m_out, int32_t* u, int32_t* v, double* w,
+                                 int outputs_on_host) {
+    gr_ctx* ctx = const_cast<gr_ctx*>(cctx);
+    if (!ctx) return set_error(nullptr, GR_EINVAL, "get_edges: ctx is NULL");
+    if (m_out) *m_out = ctx->m;
+    if (ctx->m == 0) return GR_OK;
+    cudaMemcpyKind kind = outputs_on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    if (u) GR_TRY_CUDA(ctx, cudaMemcpyAsync(u, ctx->eu, sizeof(int32_t) * ctx->m, kind, ctx->stream), "get_edges");
+    if (v) GR_TRY_CUDA(ctx, cudaMemcpyAsync(v, ctx->ev, sizeof(int32_t) * ctx->m, kind, ctx->stream), "get_edges");
+    if (w) GR_TRY_CUDA(ctx, cudaMemcpyAsync(w, ctx->ew, sizeof(double) * ctx->m, kind, ctx->stream), "get_edges");
+    if (outputs_on_host) GR_TRY_CUDA(ctx, cudaStreamSynchronize(ctx->stream), "get_edges");
+    return GR_OK;
+}
+
+gr_status graph_reduce_get_map(const gr_ctx* cctx, int32_t* agg_out, int64_t* n_parent_out) {
+    gr_ctx* ctx = const_cast<gr_ctx*>(cctx);
+    if (!ctx) return set_error(nullptr, GR_EINVAL, "get_map: ctx is NULL");
+    if (!ctx->parent_map) return set_error(ctx, GR_ESTATE, "get_map: context was not made by coarsen");
+    if (n_parent_out) *n_parent_out = ctx->parent_n;
+    if (agg_out)
+        GR_TRY_CUDA(ctx, cudaMemcpyAsync(agg_out, ctx->parent_map, sizeof(int32_t) * ctx->parent_n,
+                                         cudaMemcpyDeviceToDevice, ctx->stream), "get_map");
+    return GR_OK;
+}
+
+gr_status graph_reduce_compose_maps(gr_ctx* const* levels, int nlevels, int32_t* agg_out) {
+    if (!levels || nlevels < 1 || !levels[0] || !agg_out)
+        return set_error(nullptr, GR_EINVAL, "compose_maps: need at least one level and an output");
+    return compose_impl(levels, nlevels, agg_out);
+}
+
+gr_status graph_reduce_multilevel(gr_ctx* fine, const gr_params* p, gr_ctx** levels_out, int* nlevels_out,
+                                  gr_level_stats* stats_out) {
+    if (!fine) return set_error(nullptr, GR_EINVAL, "multilevel: ctx is NULL");
+    if (!p || !levels_out || !nlevels_out) return set_error(fine, GR_EINVAL, "multilevel: NULL argument");
+    if (!valid_K(p->K) || p->sweeps < 0 || !(p->omega > 0.0 && p->omega <= 1.0) || p->passes < 1 ||
+        p->passes > 30 || p->level_ratio < 2 || p->final_target < 1 || p->max_levels < 1 ||
+        (p->prec != GR_F64 && p->prec != GR_F32 && p->prec != GR_BF16))
+        return set_error(fine, GR_EINVAL, "multilevel: invalid parameters");
+    *nlevels_out = 0;
+    const gr_prec prec = (gr_prec)p->prec;
+    const size_t xsz = prec == GR_F64 ? 8 : (prec == GR_F32 ? 4 : 2);
+    const size_t dsz = prec == GR_F64 ? 8 : 4;
+    cudaStream_t s = fine->stream;
+    cudaEvent_t ev[7];
+    const bool timed = stats_out != nullptr;
+    if (timed)
+        for (int i = 0; i < 7; ++i) GR_TRY_CUDA(fine, cudaEventCreate(&ev[i]), "event");
+    gr_ctx* cur = fine;
+    gr_status st = GR_OK;
+    int nl = 0;
+    for (int lvl = 0; lvl < p->max_levels; ++lvl) {
+        if (cur->n <= p->final_target || cur->m == 0) break;
+        void *px, *pd, *pa;
+        cudaError_t e = fine->ws.get(WS_ML_X, xsz * (size_t)cur->n * p->K, &px);
+        if (e == cudaSuccess) e = fine->ws.get(WS_ML_D, dsz * (size_t)cur->m, &pd);
+        if (e == cudaSuccess) e = fine->ws.get(WS_ML_AGG, sizeof(int32_t) * (size_t)cur->n, &pa);
+        if (e != cudaSuccess) {
+            st = cuda_error(fine, e, "multilevel scratch");
+            break;
+        }
+        if (timed) cudaEventRecord(ev[0], s);
+        st = smooth_impl(cur, p->K, p->sweeps, p->omega, p->seed, lvl, prec, px, timed ? ev[5] : nullptr,
+                         timed ? ev[6] : nullptr);
+        if (timed) cudaEventRecord(ev[1], s);
+        if (st == GR_OK) st = affinity_impl(cur, px, p->K, prec, pd, nullptr);
+        if (timed) cudaEventRecord(ev[2], s);
+        int64_t target = (cur->n + p->level_ratio - 1) / p->level_ratio;
+        if (target < p->final_target) target = p->final_target;
+        int64_t nc = 0;
+        int32_t rounds = 0;
+        if (st == GR_OK)
+            st = aggregate_impl(cur, pd, prec == GR_F64, target, p->passes, p->max_rounds, (int32_t*)pa, &nc,
+                                &rounds);
+        if (timed) cudaEventRecord(ev[3], s);
+        if (st != GR_OK) {
+            if (cur != fine) fine->last_error = cur->last_error;
+            break;
+        }
+        if (nc == cur->n) break;  // no merge possible
+        gr_ctx* next = nullptr;
+        st = coarsen_impl(cur, (const int32_t*)pa, nc, &next);
+        if (timed) cudaEventRecord(ev[4], s);
+        if (st != GR_OK) {
+            if (cur != fine) fine->last_error = cur->last_error;
+            break;
+        }
+        if (timed) {
+            cudaEventSynchronize(ev[4]);
+            gr_level_stats& L = stats_out[nl];
+            L.n = cur->n;
+            L.m = cur->m;
+            L.nc = next->n;
+            L.mc = next->m;
+            L.rounds = rounds;
+            cudaEventElapsedTime(&L.t_smooth, ev[0], ev[1]);
+            cudaEventElapsedTime(&L.t_affinity, ev[1], ev[2]);
+            cudaEventElapsedTime(&L.t_aggregate, ev[2], ev[3]);
+            cudaEventElapsedTime(&L.t_coarsen, ev[3], ev[4]);
+            L.sweeps = p->sweeps;
+            L.t_sweeps = 0.f;
+            if (p->sweeps > 0) cudaEventElapsedTime(&L.t_sweeps, ev[5], ev[6]);
+        }
+        levels_out[nl++] = next;
+        cur = next;
+    }
+    if (timed)
+        for (int i = 0; i < 7; ++i) cudaEventDestroy(ev[i]);
+    *nlevels_out = nl;
+    return st;
+}
+
+gr_status graph_reduce_loss_fwd(gr_ctx* fine, gr_ctx* coarse, const int32_t* agg, const float* X, int K,
+                                const float* w_c, int sweeps_c, double omega, float* loss_out, float* saved) {
+    if (!fine || !coarse) return set_error(fine, GR_EINVAL, "loss_fwd: NULL context");
+    if (!agg || !X || !w_c || !loss_out || !saved) return set_error(fine, GR_EINVAL, "loss_fwd: NULL argument");
+    if (!valid_K(K) || sweeps_c < 0 || !(omega > 0.0 && omega <= 1.0))
+        return set_error(fine, GR_EINVAL, "loss_fwd: need K in {4,8,16,24,32}, sweeps >= 0, 0 < omega <= 1");
+    if (coarse->stream != fine->stream) return set_error(fine, GR_EINVAL, "loss_fwd: contexts must share a stream");
+    return loss_fwd_impl(fine, coarse, agg, X, K, w_c, sweeps_c, omega, loss_out, saved);
+}
+
+gr_status graph_reduce_loss_bwd(gr_ctx* coarse, const float* saved, int K, const float* w_c, int sweeps_c,
+                                double omega, const float* grad_loss, float* grad_w_out) {
+    if (!coarse) return set_error(nullptr, GR_EINVAL, "loss_bwd: NULL context");
+    if (!saved || !w_c || !grad_loss || !grad_w_out) return set_error(coarse, GR_EINVAL, "loss_bwd: NULL argument");
+    if (!valid_K(K) || sweeps_c < 0 || !(omega > 0.0 && omega <= 1.0))
+        return set_error(coarse, GR_EINVAL, "loss_bwd: need K in {4,8,16,24,32}, sweeps >= 0, 0 < omega <= 1");
+    return loss_bwd_impl(coarse, saved, K, w_c, sweeps_c, omega, grad_loss, grad_w_out);
+}
+
+uint64_t graph_reduce_launch_count(void) { return launch_count(); }
+
+const char* graph_reduce_last_error(const gr_ctx* ctx) {
+    return ctx ? ctx->last_error.c_str() : g_create_error.c_str();
+}
+
+void graph_reduce_destroy(gr_ctx* c) {
+    if (!c) return;
+    cudaStream_t s = c->stream;
+    void* ptrs[] = {c->eu, c->ev, c->ew, c->eptr, c->rowptr, c->col, c->eid, c->cw32, c->wn64, c->deg,
+                    c->parent_map};
+    for (void* p : ptrs)
+        if (p) cudaFreeAsync(p, s);
+    c->ws.release();
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,349 @@
+// Graph construction: the symmetric CSR of A_G and the degrees D_G (Sec. 2.1),
+// and Galerkin coarsening L_R = P^T L_G P (Sec. 3.2.2) by sort + segmented sum.
+#include "gr_internal.cuh"
+
+namespace gr {
+
+constexpr int TB = 256;
+
+// ---------------------------------------------------------------------------
+// CSR construction from a canonical edge list
+// ---------------------------------------------------------------------------
+// eptr[p] = first edge with u >= p (u is sorted), for p in [0, n]
+__global__ void k_upper_ptr(const int32_t* __restrict__ eu, int64_t m, int64_t n,
+                            int64_t* __restrict__ eptr) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e > m) return;
+    int64_t prev = e == 0 ? -1 : (int64_t)eu[e - 1];
+    int64_t cur = e == m ? n : (int64_t)eu[e];
+    for (int64_t p = prev + 1; p <= cur; ++p) eptr[p] = e;
+}
+
+__global__ void k_lower_count(const int32_t* __restrict__ ev, int64_t m, int32_t* __restrict__ lcnt) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < m) atomicAdd(&lcnt[ev[e]], 1);
+}
+
+// rowcnt[p] = lower count + upper count (entry n is 0); lc64 = lower count as int64
+__global__ void k_row_count(const int32_t* __restrict__ lcnt, const int64_t* __restrict__ eptr,
+                            int64_t n, int64_t* __restrict__ rowcnt, int64_t* __restrict__ lc64) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < n) {
+        rowcnt[p] = (int64_t)lcnt[p] + (eptr[p + 1] - eptr[p]);
+        lc64[p] = lcnt[p];
+    } else if (p == n) {
+        rowcnt[p] = 0;
+        lc64[p] = 0;
+    }
+}
+
+__global__ void k_keys_from_v(const int32_t* __restrict__ ev, int64_t m, uint32_t* __restrict__ keys,
+                              uint32_t* __restrict__ vals) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < m) {
+        keys[e] = (uint32_t)ev[e];
+        vals[e] = (uint32_t)e;
+    }
+}
+
+// lower part of row p: edges (q, p), q < p, in ascending q (= ascending id);
+// position t of the stable sort by v holds the t-th such edge overall.
+__global__ void k_fill_lower(const uint32_t* __restrict__ skey, const uint32_t* __restrict__ sval,
+                             int64_t m, const int64_t* __restrict__ lstart,
+                             const int64_t* __restrict__ rowptr, const int32_t* __restrict__ eu,
+                             const double* __restrict__ ew, int32_t* __restrict__ col,
+                             int32_t* __restrict__ eid, double* __restrict__ wslot) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= m) return;
+    int64_t p = skey[t];
+    int64_t e = sval[t];
+    int64_t slot = rowptr[p] + (t - lstart[p]);
+    col[slot] = eu[e];
+    eid[slot] = (int32_t)e;
+    wslot[slot] = ew[e];
+}
+
+// upper part of row p: edges (p, v), v > p, after the lower part
+__global__ void k_fill_upper(const int32_t* __restrict__ eu, const int32_t* __restrict__ ev,
+                             const double* __restrict__ ew, int64_t m,
+                             const int64_t* __restrict__ eptr, const int32_t* __restrict__ lcnt,
+                             const int64_t* __restrict__ rowptr, int32_t* __restrict__ col,
+                             int32_t* __restrict__ eid, double* __restrict__ wslot) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m) return;
+    int64_t p = eu[e];
+    int64_t slot = rowptr[p] + lcnt[p] + (e - eptr[p]);
+    col[slot] = ev[e];
+    eid[slot] = (int32_t)e;
+    wslot[slot] = ew[e];
+}
+
+// warp per row: D(p,p) = sum of the row's weights (fixed shuffle-tree order),
+// then the row-scaled weights w / D(p,p) that D^-1 A uses.
+__global__ void k_degree_scale(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                               int64_t n, double* __restrict__ wn64, int2* __restrict__ cw32,
+                               double* __restrict__ deg) {
+    const int lane = threadIdx.x & 31;
+    int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (p >= n) return;
+    int64_t b = rowptr[p], e = rowptr[p + 1];
+    double s = 0.0;
+    for (int64_t j = b + lane; j < e; j += 32) s += wn64[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) deg[p] = s;
+    double inv = s > 0.0 ? 1.0 / s : 0.0;
+    for (int64_t j = b + lane; j < e; j += 32) {
+        double x = wn64[j] * inv;
+        wn64[j] = x;
+        cw32[j] = make_int2(col[j], __float_as_int((float)x));
+    }
+}
+
+gr_status build_csr(gr_ctx* c) {
+    const int64_t n = c->n, m = c->m;
+    cudaStream_t s = c->stream;
+    GR_TRY_CUDA(c, cudaMallocAsync(&c->eptr, sizeof(int64_t) * (n + 1), s), "alloc eptr");
+    GR_TRY_CUDA(c, cudaMallocAsync(&c->rowptr, sizeof(int64_t) * (n + 1), s), "alloc rowptr");
+    GR_TRY_CUDA(c, cudaMallocAsync(&c->deg, sizeof(double) * (n > 0 ? n : 1), s), "alloc deg");
+    size_t slots = (size_t)(2 * m > 0 ? 2 * m : 1);
+    GR_TRY_CUDA(c, cudaMallocAsync(&c->col, sizeof(int32_t) * slots, s), "alloc col");
+    GR_TRY_CUDA(c, cudaMallocAsync(&c->eid, sizeof(int32_t) * slots, s), "alloc eid");
+    GR_TRY_CUDA(c, cudaMallocAsync(&c->cw32, sizeof(int2) * slots, s), "alloc cw32");
+    GR_TRY_CUDA(c, cudaMallocAsync(&c->wn64, sizeof(double) * slots, s), "alloc wn64");
+
+    void *p_lcnt, *p_i64;
+    GR_TRY_CUDA(c, c->ws.get(WS_COARSE_TMP, sizeof(int32_t) * (size_t)(n + 1), &p_lcnt), "ws");
+    GR_TRY_CUDA(c, c->ws.get(WS_SORT_C, sizeof(int64_t) * (size_t)(n + 1) * 3, &p_i64), "ws");
+    int32_t* lcnt = (int32_t*)p_lcnt;
+    int64_t* rowcnt = (int64_t*)p_i64;
+    int64_t* lc64 = rowcnt + (n + 1);
+    int64_t* lstart = lc64 + (n + 1);
+
+    k_upper_ptr<<<(unsigned)ceil_div(m + 1, TB), TB, 0, s>>>(c->eu, m, n, c->eptr); count_launch();
+    GR_TRY_CUDA(c, cudaMemsetAsync(lcnt, 0, sizeof(int32_t) * (size_t)(n + 1), s), "memset");
+    if (m > 0) k_lower_count<<<(unsigned)ceil_div(m, TB), TB, 0, s>>>(c->ev, m, lcnt); count_launch();
+    k_row_count<<<(unsigned)ceil_div(n + 1, TB), TB, 0, s>>>(lcnt, c->eptr, n, rowcnt, lc64); count_launch();
+    GR_TRY_CUDA(c, scan_exclusive_i64(rowcnt, c->rowptr, n + 1, c->ws, s), "scan rowptr");
+    GR_TRY_CUDA(c, scan_exclusive_i64(lc64, lstart, n + 1, c->ws, s), "scan lstart");
+    if (m > 0) {
+        // a stable sort of edge ids by v lists every row's lower part in order
+        void *p_k0, *p_v0, *p_alt;
+        GR_TRY_CUDA(c, c->ws.get(WS_SORT_A, sizeof(uint32_t) * (size_t)m, &p_k0), "ws");
+        GR_TRY_CUDA(c, c->ws.get(WS_SORT_B, sizeof(uint32_t) * (size_t)m, &p_v0), "ws");
+        GR_TRY_CUDA(c, c->ws.get(WS_SORT_D, sizeof(uint32_t) * (size_t)m * 2, &p_alt), "ws");
+        uint32_t* k0 = (uint32_t*)p_k0;
+        uint32_t* v0 = (uint32_t*)p_v0;
+        uint32_t* k1 = (uint32_t*)p_alt;
+        uint32_t* v1 = k1 + m;
+        k_keys_from_v<<<(unsigned)ceil_div(m, TB), TB, 0, s>>>(c->ev, m, k0, v0); count_launch();
+        int alt = 0;
+        GR_TRY_CUDA(c, radix_sort_u32(k0, v0, k1, v1, m, bits_for((uint64_t)(n - 1)), c->ws, s, &alt),
+                    "sort by v");
+        const uint32_t* sk = alt ? k1 : k0;
+        const uint32_t* sv = alt ? v1 : v0;
+        k_fill_lower<<<(unsigned)ceil_div(m, TB), TB, 0, s>>>(sk, sv, m, lstart, c->rowptr, c->eu,
+                                                              c->ew, c->col, c->eid, c->wn64); count_launch();
+        k_fill_upper<<<(unsigned)ceil_div(m, TB), TB, 0, s>>>(c->eu, c->ev, c->ew, m, c->eptr, lcnt,
+                                                              c->rowptr, c->col, c->eid, c->wn64); count_launch();
+    }
+    if (n > 0)
+        k_degree_scale<<<(unsigned)ceil_div(n * 32, TB), TB, 0, s>>>(c->rowptr, c->col, n, c->wn64,
+                                                                    c->cw32, c->deg); count_launch();
+    GR_TRY_CUDA(c, cudaGetLastError(), "csr kernels");
+    return GR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Galerkin coarsening
+// ---------------------------------------------------------------------------
+// key of fine edge e = (min(A,B), max(A,B)) packed as min*nc + max; an edge
+// inside one aggregate gets the sentinel nc*nc, which sorts after every pair.
+__global__ void k_galerkin_keys(const int32_t* __restrict__ eu, const int32_t* __restrict__ ev,
+                                const int32_t* __restrict__ agg, int64_t m, uint64_t nc,
+                                uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m) return;
+    uint64_t A = (uint64_t)agg[eu[e]], B = (uint64_t)agg[ev[e]];
+    uint64_t lo = A < B ? A : B, hi = A < B ? B : A;
+    keys[e] = A == B ? nc * nc : lo * nc + hi;
+    vals[e] = (uint32_t)e;
+}
+
+__global__ void k_segment_heads(const uint64_t* __restrict__ keys, int64_t m, uint64_t sentinel,
+                                int32_t* __restrict__ head) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= m) return;
+    uint64_t k = keys[t];
+    head[t] = (k != sentinel && (t == 0 || keys[t - 1] != k)) ? 1 : 0;
+}
+
+// one thread per segment head: sum the segment's fine weights in sorted order
+// (ascending fine edge id, the sort being stable) into the reduced edge.
+__global__ void k_segment_sum(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals,
+                              const int32_t* __restrict__ head, const int32_t* __restrict__ hpos,
+                              int64_t m, uint64_t nc, const double* __restrict__ ew,
+                              int32_t* __restrict__ uc, int32_t* __restrict__ vc,
+                              double* __restrict__ wc) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= m || !head[t]) return;
+    uint64_t k = keys[t];
+    double sum = 0.0;
+    for (int64_t j = t; j < m && keys[j] == k; ++j) sum += ew[vals[j]];
+    int64_t r = hpos[t];
+    uc[r] = (int32_t)(k / nc);
+    vc[r] = (int32_t)(k % nc);
+    wc[r] = sum;
+}
+
+__global__ void k_total_i32(const int32_t* __restrict__ flag, const int32_t* __restrict__ pos,
+                            int64_t m, int64_t* __restrict__ out) {
+    *out = m > 0 ? (int64_t)pos[m - 1] + flag[m - 1] : 0;
+}
+
+__global__ void k_check_labels(const int32_t* __restrict__ agg, int64_t n, int64_t nc,
+                               int32_t* __restrict__ used, int32_t* __restrict__ bad) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int32_t a = agg[i];
+    if (a < 0 || a >= nc) atomicExch(bad, 1);
+    else used[a] = 1;
+}
+
+__global__ void k_check_used(const int32_t* __restrict__ used, int64_t nc, int32_t* __restrict__ bad) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nc && !used[i]) atomicExch(bad, 1);
+}
+
+gr_status coarsen_impl(gr_ctx* c, const int32_t* agg, int64_t nc, gr_ctx** out) {
+    const int64_t n = c->n, m = c->m;
+    cudaStream_t s = c->stream;
+    int64_t* hs = host_scratch();
+    if (!hs) return set_error(c, GR_ENOMEM, "coarsen: pinned scratch unavailable");
+    if (nc < 1 || nc > n) return set_error(c, GR_EINVAL, "coarsen: nc must be in [1, n]");
+    if ((uint64_t)nc > (1ull << 31)) return set_error(c, GR_EINVAL, "coarsen: nc too large");
+    // labels must lie in [0, nc) and all be used
+    void* p_chk;
+    GR_TRY_CUDA(c, c->ws.get(WS_COARSE_TMP, sizeof(int32_t) * (size_t)(nc + 2), &p_chk), "ws");
+    int32_t* used = (int32_t*)p_chk;
+    int32_t* bad = used + nc;
+    GR_TRY_CUDA(c, cudaMemsetAsync(used, 0, sizeof(int32_t) * (size_t)(nc + 1), s), "memset");
+    k_check_labels<<<(unsigned)ceil_div(n, TB), TB, 0, s>>>(agg, n, nc, used, bad); count_launch();
+    k_check_used<<<(unsigned)ceil_div(nc, TB), TB, 0, s>>>(used, nc, bad); count_launch();
+
+    gr_ctx* cc = new gr_ctx();
+    cc->stream = s;
+    cc->device = c->device;
+    cc->num_sms = c->num_sms;
+    cc->ws.stream = s;
+    cc->n = nc;
+    auto fail = [&](gr_status st) {
+        graph_reduce_destroy(cc);
+        return st;
+    };
+    int64_t mc = 0;
+    if (m > 0) {
+        void *p_k, *p_v, *p_head;
+        GR_TRY_CUDA(c, c->ws.get(WS_COARSE_KEYS, sizeof(uint64_t) * (size_t)m * 2, &p_k), "ws");
+        GR_TRY_CUDA(c, c->ws.get(WS_COARSE_VALS, sizeof(uint32_t) * (size_t)m * 2, &p_v), "ws");
+        GR_TRY_CUDA(c, c->ws.get(WS_SORT_A, sizeof(int32_t) * (size_t)m * 2, &p_head), "ws");
+        uint64_t* k0 = (uint64_t*)p_k;
+        uint64_t* k1 = k0 + m;
+        uint32_t* v0 = (uint32_t*)p_v;
+        uint32_t* v1 = v0 + m;
+        int32_t* head = (int32_t*)p_head;
+        int32_t* hpos = head + m;
+        const uint64_t sentinel = (uint64_t)nc * (uint64_t)nc;
+        k_galerkin_keys<<<(unsigned)ceil_div(m, TB), TB, 0, s>>>(c->eu, c->ev, agg, m, (uint64_t)nc, k0, v0); count_launch();
+        int alt = 0;
+        GR_TRY_CUDA(c, radix_sort_u64(k0, v0, k1, v1, m, bits_for(sentinel), c->ws, s, &alt), "sort keys");
+        const uint64_t* sk = alt ? k1 : k0;
+        const uint32_t* sv = alt ? v1 : v0;
+        k_segment_heads<<<(unsigned)ceil_div(m, TB), TB, 0, s>>>(sk, m, sentinel, head); count_launch();
+        GR_TRY_CUDA(c, scan_exclusive_i32(head, hpos, m, c->ws, s), "scan heads");
+        k_total_i32<<<1, 1, 0, s>>>(head, hpos, m, hs); count_launch();
+        GR_TRY_CUDA(c, cudaGetLastError(), "galerkin kernels");
+        GR_TRY_CUDA(c, cudaMemcpyAsync(hs + 1, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s),
+                    "copy");
+        GR_TRY_CUDA(c, cudaStreamSynchronize(s), "sync");
+        mc = hs[0];
+        if (((int32_t*)(hs + 1))[0]) {
+            delete cc;
+            return set_error(c, GR_EINVAL, "coarsen: labels must lie in [0, nc) and all be used");
+        }
+        cc->m = mc;
+        cudaError_t e1 = cudaMallocAsync(&cc->eu, sizeof(int32_t) * (size_t)(mc > 0 ? mc : 1), s);
+        cudaError_t e2 = cudaMallocAsync(&cc->ev, sizeof(int32_t) * (size_t)(mc > 0 ? mc : 1), s);
+        cudaError_t e3 = cudaMallocAsync(&cc->ew, sizeof(double) * (size_t)(mc > 0 ? mc : 1), s);
+        if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+            set_error(c, GR_ENOMEM, "coarsen: allocation failed");
+            return fail(GR_ENOMEM);
+        }
+        k_segment_sum<<<(unsigned)ceil_div(m, TB), TB, 0, s>>>(sk, sv, head, hpos, m, (uint64_t)nc,
+                                                               c->ew, cc->eu, cc->ev, cc->ew); count_launch();
+        GR_TRY_CUDA(c, cudaGetLastError(), "segment sum");
+    } else {
+        hs[1] = 0;
+        GR_TRY_CUDA(c, cudaMemcpyAsync(hs + 1, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s),
+                    "copy");
+        GR_TRY_CUDA(c, cudaStreamSynchronize(s), "sync");
+        if (((int32_t*)(hs + 1))[0]) {
+            delete cc;
+            return set_error(c, GR_EINVAL, "coarsen: labels must lie in [0, nc) and all be used");
+        }
+        cc->m = 0;
+        cudaMallocAsync(&cc->eu, 4, s);
+        cudaMallocAsync(&cc->ev, 4, s);
+        cudaMallocAsync(&cc->ew, 8, s);
+    }
+    gr_status st = build_csr(cc);
+    if (st != GR_OK) {
+        set_error(c, st, "coarsen: " + cc->last_error);
+        return fail(st);
+    }
+    if (cudaMallocAsync(&cc->parent_map, sizeof(int32_t) * (size_t)(n > 0 ? n : 1), s) != cudaSuccess) {
+        set_error(c, GR_ENOMEM, "coarsen: allocation failed");
+        return fail(GR_ENOMEM);
+    }
+    GR_TRY_CUDA(c, cudaMemcpyAsync(cc->parent_map, agg, sizeof(int32_t) * (size_t)n,
+                                   cudaMemcpyDeviceToDevice, s), "copy map");
+    cc->parent_n = n;
+    *out = cc;
+    return GR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Map composition (fine -> coarsest)
+// ---------------------------------------------------------------------------
+struct MapChain {
+    const int32_t* map[64];
+    int count;
+};
+
+__global__ void k_compose(MapChain chain, int64_t n, int32_t* __restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int32_t x = (int32_t)i;
+    for (int l = 0; l < chain.count; ++l) x = chain.map[l][x];
+    out[i] = x;
+}
+
+gr_status compose_impl(gr_ctx* const* levels, int nlevels, int32_t* out) {
+    gr_ctx* c0 = levels[0];
+    if (nlevels > 64) return set_error(c0, GR_EINVAL, "compose: at most 64 levels");
+    MapChain ch;
+    ch.count = nlevels;
+    for (int l = 0; l < nlevels; ++l) {
+        if (!levels[l] || !levels[l]->parent_map)
+            return set_error(c0, GR_ESTATE, "compose: every level must come from coarsen");
+        if (l > 0 && levels[l]->parent_n != levels[l - 1]->n)
+            return set_error(c0, GR_EINVAL, "compose: levels do not chain");
+        ch.map[l] = levels[l]->parent_map;
+    }
+    int64_t n = c0->parent_n;
+    if (n > 0) k_compose<<<(unsigned)ceil_div(n, TB), TB, 0, c0->stream>>>(ch, n, out); count_launch();
+    GR_TRY_CUDA(c0, cudaGetLastError(), "compose");
+    return GR_OK;
+}
+
+}  // namespace gr

@@ -1,0 +1,129 @@
+// Internal declarations shared by the translation units of libgraphreduce.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "graph_reduce.h"
+
+namespace gr {
+
+// ---------------------------------------------------------------------------
+// Error plumbing: every internal routine returns cudaError_t or gr_status;
+// the API layer turns CUDA errors into GR_ECUDA with a message.
+// ---------------------------------------------------------------------------
+#define GR_CUDA(expr)                                   \
+    do {                                                \
+        cudaError_t _e = (expr);                        \
+        if (_e != cudaSuccess) return _e;               \
+    } while (0)
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Grow-only device scratch, stream-ordered (cudaMallocAsync / cudaFreeAsync).
+struct Workspace {
+    struct Slot {
+        void* ptr = nullptr;
+        size_t bytes = 0;
+    };
+    std::vector<Slot> slots;
+    cudaStream_t stream = nullptr;
+    cudaError_t get(int slot, size_t bytes, void** out);
+    void release();
+};
+
+// Named workspace slots (each owner uses disjoint slots).
+enum WsSlot {
+    WS_SORT_A = 0, WS_SORT_B, WS_SORT_C, WS_SORT_D, WS_SORT_HIST, WS_SCAN,
+    WS_SMOOTH_BUF, WS_SMOOTH_STATS, WS_SMOOTH_PART,
+    WS_AGG_STATE, WS_AGG_LIST, WS_AGG_KEYS, WS_AGG_SMALL,
+    WS_COARSE_KEYS, WS_COARSE_VALS, WS_COARSE_TMP,
+    WS_LOSS_A, WS_LOSS_B, WS_LOSS_C,
+    WS_ML_X, WS_ML_D, WS_ML_AGG,
+    WS_PINNED_UNUSED,
+    WS_COUNT
+};
+
+}  // namespace gr
+
+struct gr_ctx {
+    int64_t n = 0, m = 0;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int num_sms = 0;
+    // canonical edge list (owned)
+    int32_t* eu = nullptr;
+    int32_t* ev = nullptr;
+    double* ew = nullptr;
+    int64_t* eptr = nullptr;    // n+1: edges with u == p are [eptr[p], eptr[p+1])
+    // symmetric CSR; row order = ascending neighbour = ascending edge id
+    int64_t* rowptr = nullptr;  // n+1
+    int32_t* col = nullptr;     // 2m
+    int32_t* eid = nullptr;     // 2m
+    int2* cw32 = nullptr;       // 2m: (col, float bits of w / deg_row)
+    double* wn64 = nullptr;     // 2m: w / deg_row
+    double* deg = nullptr;      // n
+    // mapping from the parent level (coarse contexts only)
+    int32_t* parent_map = nullptr;
+    int64_t parent_n = 0;
+    gr::Workspace ws;
+    std::string last_error;
+};
+
+namespace gr {
+
+// primitives (gr_prims.cu)
+cudaError_t scan_exclusive_i64(const int64_t* in, int64_t* out, int64_t count, Workspace& ws,
+                               cudaStream_t s);
+cudaError_t scan_exclusive_i32(const int32_t* in, int32_t* out, int64_t count, Workspace& ws,
+                               cudaStream_t s);
+// Stable LSD radix sort of (key, value) pairs on the low `bits` key bits.
+// Buffers a/b ping-pong; on return *result points at the buffers holding the
+// sorted data (either the inputs or the alternates).
+cudaError_t radix_sort_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
+                           uint32_t* vals_alt, int64_t count, int bits, Workspace& ws,
+                           cudaStream_t s, int* result_in_alt);
+cudaError_t radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt,
+                           uint32_t* vals_alt, int64_t count, int bits, Workspace& ws,
+                           cudaStream_t s, int* result_in_alt);
+int bits_for(uint64_t max_value_inclusive);
+// 64 bytes of pinned host memory owned by the calling thread, for small
+// readbacks inside one API call (never held across calls).
+int64_t* host_scratch();
+// keep freed stream-ordered allocations cached in the device's default pool
+void tune_mempool(int device);
+// process-wide count of kernel launches made by this library
+void count_launch();
+uint64_t launch_count();
+
+// graph construction (gr_graph.cu)
+gr_status build_csr(gr_ctx* c);
+
+// kernels entry points used by the API layer
+// ev_begin / ev_end (optional) are recorded around the sweep kernels only
+gr_status smooth_impl(gr_ctx* c, int K, int sweeps, double omega, uint64_t seed, int level,
+                      gr_prec prec, void* X, cudaEvent_t ev_begin = nullptr,
+                      cudaEvent_t ev_end = nullptr);
+gr_status affinity_impl(gr_ctx* c, const void* X, int K, gr_prec prec, void* d, void* a);
+gr_status aggregate_impl(gr_ctx* c, const void* d, int d_is_f64, int64_t target_nc, int passes,
+                         int max_rounds, int32_t* agg, int64_t* nc_out, int32_t* rounds_out);
+gr_status coarsen_impl(gr_ctx* c, const int32_t* agg, int64_t nc, gr_ctx** out);
+gr_status loss_fwd_impl(gr_ctx* fine, gr_ctx* coarse, const int32_t* agg, const float* X, int K,
+                        const float* w_c, int sweeps, double omega, float* loss, float* saved);
+gr_status loss_bwd_impl(gr_ctx* coarse, const float* saved, int K, const float* w_c, int sweeps,
+                        double omega, const float* grad_loss, float* grad_w);
+
+gr_status set_error(gr_ctx* c, gr_status st, const std::string& msg);
+gr_status cuda_error(gr_ctx* c, cudaError_t e, const char* where);
+
+}  // namespace gr
+
+#define GR_TRY_CUDA(ctx, expr, where)                                   \
+    do {                                                                \
+        cudaError_t _e = (expr);                                        \
+        if (_e != cudaSuccess) return gr::cuda_error((ctx), _e, where); \
+    } while (0)

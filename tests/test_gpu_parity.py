@@ -1,0 +1,297 @@
+"""GPU parity: every C-ABI call against the FP64 oracle on the same seeded
+inputs.  Bars (from the benchmark spec of the reduction's accuracy):
+  smoothed X         per-column |dX|/|X| <= 1e-12 (FP64), <= 1e-5 (FP32)
+  BF16-stored X      reported, not gated (bfloat16 keeps ~3 digits)
+  distance d         FP64 bit-exact given the same X; FP32 |dd| <= 1e-5
+  aggregates         bit-exact given the oracle's (or any shared) distances
+  reduced graph      pattern bit-exact, weights <= 1e-6 relative
+  10 eigenvalues     <= 1e-3 relative to the oracle's reduced graph
+"""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def gr():
+    from paper_1812_08942_gb300 import build as B
+    B.build()
+    import paper_1812_08942_gb300 as gr
+    gr.load()
+    return gr
+
+
+def _col_relerr(A, B):
+    A = np.asarray(A, np.float64)
+    B = np.asarray(B, np.float64)
+    return np.linalg.norm(A - B, axis=0) / np.maximum(np.linalg.norm(B, axis=0), 1e-300)
+
+
+GRAPHS = {
+    "grid13x9": lambda: W.grid2d(13, 9),
+    "rand_w": lambda: W.random_sparse(1537, 6000, seed=3),
+    "star": lambda: W.star(200),
+    "complete": lambda: W.complete(40, 0.5),
+    "path_iso": lambda: W.Graph(300, np.arange(0, 250, dtype=np.int32), np.arange(1, 251, dtype=np.int32),
+                                np.linspace(0.5, 2.0, 250)),  # nodes 251..299 isolated
+    "mesh_ln": lambda: W.mesh3d(11, 7, 5, seed=4),
+}
+
+
+# ---------------------------------------------------------------------------
+# create / edges round trip / input validation
+# ---------------------------------------------------------------------------
+def test_create_roundtrip_and_validation(gr, oracle_mod):
+    g = W.random_sparse(777, 3000, seed=1)
+    G = gr.graph_reduce_create(g.n, g.u, g.v, g.w)
+    u, v, w = gr.graph_reduce_get_edges(G, on_host=True)
+    assert np.array_equal(u.numpy(), g.u) and np.array_equal(v.numpy(), g.v) and np.array_equal(w.numpy(), g.w)
+    # device inputs
+    G2 = gr.graph_reduce_create(g.n, torch.from_numpy(g.u).to(DEV), torch.from_numpy(g.v).to(DEV),
+                                torch.from_numpy(g.w).to(DEV))
+    u2, _, _ = gr.graph_reduce_get_edges(G2)
+    assert torch.equal(u2.cpu(), torch.from_numpy(g.u))
+    bad = [
+        (g.v, g.u, g.w),                                   # u > v
+        (g.u[::-1].copy(), g.v[::-1].copy(), g.w),         # unsorted
+        (g.u, g.v, -g.w),                                  # negative weight
+        (np.concatenate([g.u, g.u[-1:]]), np.concatenate([g.v, g.v[-1:]]), np.concatenate([g.w, g.w[-1:]])),
+    ]
+    for bu, bv, bw in bad:
+        for dev_inputs in (False, True):
+            args = [np.ascontiguousarray(x) for x in (bu, bv, bw)]
+            if dev_inputs:
+                args = [torch.from_numpy(a).to(DEV) for a in args]
+            with pytest.raises(gr.GraphReduceError) as ei:
+                gr.graph_reduce_create(g.n, *args)
+            assert ei.value.status == 1
+
+
+# ---------------------------------------------------------------------------
+# smoothing
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("name", list(GRAPHS))
+@pytest.mark.parametrize("K", [4, 8, 16, 24, 32])
+def test_smooth_parity_f64_f32(gr, oracle_mod, name, K):
+    g = GRAPHS[name]()
+    S, omega, seed, level = 5, 0.7, 7, 2
+    ref = oracle_mod.smooth(g.n, g.u, g.v, g.w, K, S, omega, seed, level)
+    G = gr.graph_reduce_create(g.n, g.u, g.v, g.w)
+    X64 = torch.empty(g.n, K, dtype=torch.float64, device=DEV)
+    gr.graph_reduce_smooth(G, X64, S, omega, seed, level)
+    e64 = _col_relerr(X64.cpu().numpy(), ref)
+    assert e64.max() <= 1e-12, e64.max()
+    X32 = torch.empty(g.n, K, dtype=torch.float32, device=DEV)
+    gr.graph_reduce_smooth(G, X32, S, omega, seed, level)
+    e32 = _col_relerr(X32.cpu().numpy(), ref)
+    assert e32.max() <= 1e-5, e32.max()
+    # deterministic: a second run is bitwise identical
+    X32b = torch.empty_like(X32)
+    gr.graph_reduce_smooth(G, X32b, S, omega, seed, level)
+    assert torch.equal(X32, X32b)
+
+
+@pytest.mark.parametrize("K", [8, 16, 24])
+def test_smooth_bf16_reported(gr, oracle_mod, K):
+    g = W.grid2d(64, 64)
+    ref = oracle_mod.smooth(g.n, g.u, g.v, g.w, K, 5)
+    G = gr.graph_reduce_create(g.n, g.u, g.v, g.w)
+    X = torch.empty(g.n, K, dtype=torch.bfloat16, device=DEV)
+    gr.graph_reduce_smooth(G, X, 5)
+    e = _col_relerr(X.float().cpu().numpy(), ref)
+    print("bf16 storage K=%d: max per-column relative error %.3e" % (K, e.max()))
+    assert e.max() < 3e-2
+
+
+def test_smooth_zero_sweeps_and_edgeless(gr, oracle_mod):
+    # no sweep: the centred, normalised random block itself
+    g = W.grid2d(10, 10)
+    G = gr.graph_reduce_create(g.n, g.u, g.v, g.w)
+    X = torch.empty(g.n, 8, dtype=torch.float64, device=DEV)
+    gr.graph_reduce_smooth(G, X, 0, 0.7, 3, 1)
+    ref = oracle_mod.center_normalize(oracle_mod.test_vectors_raw(g.n, 8, 3, 1))
+    assert _col_relerr(X.cpu().numpy(), ref).max() <= 1e-13
+    # a graph without edges: every node is isolated and keeps its value
+    E = gr.graph_reduce_create(50, np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0))
+    X = torch.empty(50, 4, dtype=torch.float64, device=DEV)
+    gr.graph_reduce_smooth(E, X, 3)
+    ref = oracle_mod.smooth(50, np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0), 4, 3)
+    assert _col_relerr(X.cpu().numpy(), ref).max() <= 1e-13
+
+
+# ---------------------------------------------------------------------------
+# affinity
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("K", [4, 8, 16, 24, 32])
+def test_affinity_parity(gr, oracle_mod, K):
+    g = W.random_sparse(3001, 12000, seed=5)
+    X = oracle_mod.smooth(g.n, g.u, g.v, g.w, K, 4)
+    X[17] = 0.0  # a zero row: a = 0, d = 1
+    dref, aref = oracle_mod.affinity(g.n, g.u, g.v, X, want_a=True)
+    G = gr.graph_reduce_create(g.n, g.u, g.v, g.w)
+    Xd = torch.from_numpy(X).to(DEV)
+    d = torch.empty(g.m, dtype=torch.float64, device=DEV)
+    a = torch.empty(g.m, dtype=torch.float64, device=DEV)
+    gr.graph_reduce_affinity(G, Xd, d, a)
+    assert np.array_equal(d.cpu().numpy(), dref)  # FP64: bit-exact given the same X
+    assert np.array_equal(a.cpu().numpy(), aref)
+    d32 = torch.empty(g.m, dtype=torch.float32, device=DEV)
+    gr.graph_reduce_affinity(G, Xd.float(), d32)
+    dref32 = oracle_mod.affinity(g.n, g.u, g.v, Xd.float().double().cpu().numpy())
+    err = np.abs(d32.cpu().numpy().astype(np.float64) - dref32).max()
+    assert err <= 1e-5, err
+
+
+# ---------------------------------------------------------------------------
+# aggregation: bit-exact given the oracle's distances
+# ---------------------------------------------------------------------------
+AGG_CASES = [
+    ("grid", lambda: W.grid2d(64, 64), 1024, 2),
+    ("grid_trunc", lambda: W.grid2d(40, 30), 500, 2),
+    ("rand", lambda: W.random_sparse(5003, 20000, seed=8), 1250, 2),
+    ("rand3", lambda: W.random_sparse(2000, 9000, seed=9), 1, 3),
+    ("star", lambda: W.star(300), 1, 2),
+    ("path_iso", GRAPHS["path_iso"], 1, 2),
+    ("mesh", lambda: W.mesh3d(12, 10, 9, seed=2), 270, 2),
+]
+
+
+@pytest.mark.parametrize("case", AGG_CASES, ids=[c[0] for c in AGG_CASES])
+def test_aggregate_bitexact_oracle_d(gr, oracle_mod, case):
+    _, make, target, passes = case
+    g = make()
+    X = oracle_mod.smooth(g.n, g.u, g.v, g.w, 8, 5)
+    d = oracle_mod.affinity(g.n, g.u, g.v, X)
+    ref, rnc = oracle_mod.aggregate(g.n, g.u, g.v, d, target, passes)
+    G = gr.graph_reduce_create(g.n, g.u, g.v, g.w)
+    agg, nc, rounds = gr.graph_reduce_aggregate(G, torch.from_numpy(d).to(DEV), target, passes)
+    assert nc == rnc
+    assert np.array_equal(agg.cpu().numpy(), ref)
+    # FP32 keys: the same order as the oracle run on the FP32-rounded distances
+    d32 = d.astype(np.float32)
+    ref32, rnc32 = oracle_mod.aggregate(g.n, g.u, g.v, d32.astype(np.float64), target, passes)
+    agg32, nc32, _ = gr.graph_reduce_aggregate(G, torch.from_numpy(d32).to(DEV), target, passes)
+    assert nc32 == rnc32 and np.array_equal(agg32.cpu().numpy(), ref32)
+
+
+def test_aggregate_ties_and_errors(gr, oracle_mod):
+    g = W.grid2d(30, 30)
+    d = np.round(np.random.default_rng(1).uniform(size=g.m), 1)  # heavy ties -> edge id decides
+    G = gr.graph_reduce_create(g.n, g.u, g.v, g.w)
+    for passes, target in ((1, 1), (2, 225), (3, 1)):
+        ref, rnc = oracle_mod.aggregate(g.n, g.u, g.v, d, target, passes)
+        agg, nc, _ = gr.graph_reduce_aggregate(G, torch.from_numpy(d).to(DEV), target, passes)
+        assert nc == rnc and np.array_equal(agg.cpu().numpy(), ref)
+    # a path with increasing distances needs one round per merge: the round
+    # limit turns that into GR_ETIMEOUT instead of running on
+    p = W.path(64)
+    P = gr.graph_reduce_create(p.n, p.u, p.v, p.w)
+    dp = torch.linspace(0.01, 0.9, p.m, dtype=torch.float64, device=DEV)
+    with pytest.raises(gr.GraphReduceError) as ei:
+        gr.graph_reduce_aggregate(P, dp, 1, 1, max_rounds=3)
+    assert ei.value.status == 4
+    agg, nc, rounds = gr.graph_reduce_aggregate(P, dp, 1, 1)
+    ref, rnc = oracle_mod.aggregate(p.n, p.u, p.v, dp.cpu().numpy(), 1, 1)
+    assert nc == rnc and np.array_equal(agg.cpu().numpy(), ref) and rounds >= 32
+    with pytest.raises(gr.GraphReduceError) as ei:
+        gr.graph_reduce_aggregate(P, -dp, 1, 1)
+    assert ei.value.status == 1
+
+
+# ---------------------------------------------------------------------------
+# Galerkin coarsening: pattern bit-exact, weights <= 1e-6 relative
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("case", AGG_CASES[:4] + AGG_CASES[5:], ids=[c[0] for c in AGG_CASES[:4] + AGG_CASES[5:]])
+def test_coarsen_parity(gr, oracle_mod, case):
+    _, make, target, passes = case
+    g = make()
+    X = oracle_mod.smooth(g.n, g.u, g.v, g.w, 8, 5)
+    d = oracle_mod.affinity(g.n, g.u, g.v, X)
+    agg, nc = oracle_mod.aggregate(g.n, g.u, g.v, d, target, passes)
+    uc, vc, wc = oracle_mod.coarsen(g.n, g.u, g.v, g.w, agg, nc)
+    G = gr.graph_reduce_create(g.n, g.u, g.v, g.w)
+    C = gr.graph_reduce_coarsen(G, torch.from_numpy(agg).to(DEV), nc)
+    assert C.n == nc and C.m == len(uc)
+    gu, gv, gw = (t.numpy() for t in gr.graph_reduce_get_edges(C, on_host=True))
+    assert np.array_equal(gu, uc) and np.array_equal(gv, vc)
+    assert np.max(np.abs(gw - wc) / wc) <= 1e-6
+    assert np.array_equal(gw, wc)  # same summation order: exact
+    assert np.array_equal(gr.graph_reduce_get_map(C).cpu().numpy(), agg)
+
+
+def test_coarsen_rejects_bad_labels(gr):
+    g = W.grid2d(8, 8)
+    G = gr.graph_reduce_create(g.n, g.u, g.v, g.w)
+    agg = torch.zeros(g.n, dtype=torch.int32, device=DEV)
+    agg[5] = 3  # labels 1 and 2 unused
+    with pytest.raises(gr.GraphReduceError):
+        gr.graph_reduce_coarsen(G, agg, 4)
+    agg[5] = 9
+    with pytest.raises(gr.GraphReduceError):
+        gr.graph_reduce_coarsen(G, agg, 4)
+
+
+# ---------------------------------------------------------------------------
+# level loop, FP64 end to end against the oracle's reduction
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("shape,final", [((64, 64), 1024), ((160, 120), 700)])
+def test_multilevel_f64_eigs(gr, oracle_mod, shape, final):
+    g = W.grid2d(*shape)
+    K, S = 8, 5
+    levels = oracle_mod.reduce_multilevel(g.n, g.u, g.v, g.w, K, S, final_target=final)
+    G = gr.graph_reduce_create(g.n, g.u, g.v, g.w)
+    p = gr.ReduceParams(K=K, sweeps=S, prec=gr.GR_F64, final_target=final)
+    glev, stats = gr.graph_reduce_multilevel(G, p)
+    assert len(glev) == len(levels)
+    for lv, gl in zip(levels, glev):
+        assert gl.n == lv.nc and gl.m == len(lv.uc)
+        assert np.array_equal(gr.graph_reduce_get_map(gl).cpu().numpy(), lv.agg)
+    u, v, w = (t.numpy() for t in gr.graph_reduce_get_edges(glev[-1], on_host=True))
+    ev_gpu = oracle_mod.smallest_nontrivial_eigs(glev[-1].n, u, v, w, 10)
+    last = levels[-1]
+    ev_ref = oracle_mod.smallest_nontrivial_eigs(last.nc, last.uc, last.vc, last.wc, 10)
+    assert np.max(np.abs(ev_gpu - ev_ref) / ev_ref) <= 1e-3
+    comp = gr.graph_reduce_compose_maps(glev).cpu().numpy()
+    assert np.array_equal(comp, oracle_mod.compose_maps(levels))
+    assert all(s["rounds"] > 0 for s in stats)
+
+
+# ---------------------------------------------------------------------------
+# spectral-mismatch loss and its adjoint
+# ---------------------------------------------------------------------------
+def _loss_setup(gr, oracle_mod, n=2000, K=16, seed=31):
+    g = W.random_sparse(n, 6 * n, seed=seed)
+    levels = oracle_mod.reduce_multilevel(g.n, g.u, g.v, g.w, 8, 5, final_target=max(n // 32, 8))
+    agg = oracle_mod.compose_maps(levels)
+    last = levels[-1]
+    X = oracle_mod.smooth(g.n, g.u, g.v, g.w, K, 5, seed=1)
+    return g, X, agg, last
+
+
+@pytest.mark.parametrize("S", [0, 1, 5])
+def test_loss_and_adjoint_parity(gr, oracle_mod, S):
+    g, X, agg, last = _loss_setup(gr, oracle_mod)
+    rng = np.random.default_rng(2)
+    wc = last.wc * rng.uniform(0.5, 2.0, size=len(last.wc))  # free weights
+    L_ref, g_ref, _, _ = oracle_mod.loss(g.n, g.u, g.v, g.w, last.nc, last.uc, last.vc, wc, agg, X, S)
+    F = gr.graph_reduce_create(g.n, g.u, g.v, g.w)
+    C = gr.graph_reduce_create(last.nc, last.uc, last.vc, last.wc)
+    Xd = torch.from_numpy(X).float().to(DEV)
+    aggd = torch.from_numpy(agg).to(DEV)
+    w = torch.from_numpy(wc).float().to(DEV)
+    loss, saved = gr.graph_reduce_loss_fwd(F, C, aggd, Xd, w, S)
+    assert abs(loss.item() - L_ref) <= 1e-4 * abs(L_ref) + 1e-7
+    gw = gr.graph_reduce_loss_bwd(C, saved, X.shape[1], w, S, 0.7, torch.ones(1, device=DEV)).cpu().numpy()
+    err = np.linalg.norm(gw - g_ref) / np.linalg.norm(g_ref)
+    assert err <= 1e-4, err
+    # through torch.autograd
+    wt = w.clone().requires_grad_(True)
+    lt = gr.spectral_mismatch_loss(wt, F, C, aggd, Xd, S, 0.7)
+    (3.0 * lt).backward()
+    assert torch.allclose(wt.grad, 3.0 * torch.from_numpy(gw).to(DEV), rtol=1e-5, atol=1e-6 * float(np.abs(gw).max()))

@@ -36,6 +36,18 @@ class Graph:
         return int(self.u.shape[0])
 
 
+def sorted_unique(k):
+    """Sorted distinct values of an int64 array (np.sort + run heads; much
+    faster than np.unique on large inputs)."""
+    s = np.sort(np.asarray(k, np.int64), kind="stable")
+    if s.shape[0] == 0:
+        return s
+    head = np.empty(s.shape[0], bool)
+    head[0] = True
+    np.not_equal(s[1:], s[:-1], out=head[1:])
+    return s[head]
+
+
 def canonicalize(n, a, b, w=None, combine="first"):
     """Turn an arbitrary undirected pair list into the canonical form: drop
     self-loops, orient u < v, sort by (u, v), merge duplicates.  ``combine``
@@ -188,8 +200,9 @@ def chung_lu(n: int = 434_000, m_target: int = 16_000_000, mean_deg: float = 73.
     rng = np.random.Generator(np.random.PCG64(seed))
     keys = np.empty(0, np.int64)
     need = m_target
+    margin = 1.12
     while need > 0:
-        batch = int(need * 1.08) + 1024
+        batch = int(need * margin) + 1024
         a = np.searchsorted(cdf, rng.random(batch), side="right").astype(np.int64)
         b = np.searchsorted(cdf, rng.random(batch), side="right").astype(np.int64)
         np.minimum(a, n - 1, out=a)
@@ -197,10 +210,16 @@ def chung_lu(n: int = 434_000, m_target: int = 16_000_000, mean_deg: float = 73.
         keep = a != b
         a, b = a[keep], b[keep]
         k = np.minimum(a, b) * np.int64(n) + np.maximum(a, b)
-        keys = np.unique(np.concatenate([keys, k]))
+        keys = sorted_unique(np.concatenate([keys, k]))
         need = m_target - keys.shape[0]
-    keys = keys[:m_target] if keys.shape[0] > m_target else keys
-    # keys are sorted and unique; truncation keeps the canonical order
+        margin = 2.0
+    if keys.shape[0] > m_target:
+        # drop a uniformly random surplus (keeps the degree profile unbiased)
+        drop = rng.choice(keys.shape[0], keys.shape[0] - m_target, replace=False)
+        mask = np.ones(keys.shape[0], bool)
+        mask[drop] = False
+        keys = keys[mask]
+    # keys stay sorted and unique: the list is canonical
     u = (keys // n).astype(np.int32)
     v = (keys % n).astype(np.int32)
     return Graph(n, u, v, np.ones(u.shape[0]), "chunglu_%d" % n)
