@@ -122,7 +122,10 @@ gr_status build_csr(gr_ctx* c) {
 
     k_upper_ptr<<<(unsigned)ceil_div(m + 1, TB), TB, 0, s>>>(c->eu, m, n, c->eptr); count_launch();
     GR_TRY_CUDA(c, cudaMemsetAsync(lcnt, 0, sizeof(int32_t) * (size_t)(n + 1), s), "memset");
-    if (m > 0) k_lower_count<<<(unsigned)ceil_div(m, TB), TB, 0, s>>>(c->ev, m, lcnt); count_launch();
+    if (m > 0) {
+        k_lower_count<<<(unsigned)ceil_div(m, TB), TB, 0, s>>>(c->ev, m, lcnt);
+        count_launch();
+    }
     k_row_count<<<(unsigned)ceil_div(n + 1, TB), TB, 0, s>>>(lcnt, c->eptr, n, rowcnt, lc64); count_launch();
     GR_TRY_CUDA(c, scan_exclusive_i64(rowcnt, c->rowptr, n + 1, c->ws, s), "scan rowptr");
     GR_TRY_CUDA(c, scan_exclusive_i64(lc64, lstart, n + 1, c->ws, s), "scan lstart");
@@ -147,9 +150,11 @@ gr_status build_csr(gr_ctx* c) {
         k_fill_upper<<<(unsigned)ceil_div(m, TB), TB, 0, s>>>(c->eu, c->ev, c->ew, m, c->eptr, lcnt,
                                                               c->rowptr, c->col, c->eid, c->wn64); count_launch();
     }
-    if (n > 0)
+    if (n > 0) {
         k_degree_scale<<<(unsigned)ceil_div(n * 32, TB), TB, 0, s>>>(c->rowptr, c->col, n, c->wn64,
-                                                                    c->cw32, c->deg); count_launch();
+                                                                    c->cw32, c->deg);
+        count_launch();
+    }
     GR_TRY_CUDA(c, cudaGetLastError(), "csr kernels");
     return GR_OK;
 }
@@ -341,7 +346,10 @@ gr_status compose_impl(gr_ctx* const* levels, int nlevels, int32_t* out) {
         ch.map[l] = levels[l]->parent_map;
     }
     int64_t n = c0->parent_n;
-    if (n > 0) k_compose<<<(unsigned)ceil_div(n, TB), TB, 0, c0->stream>>>(ch, n, out); count_launch();
+    if (n > 0) {
+        k_compose<<<(unsigned)ceil_div(n, TB), TB, 0, c0->stream>>>(ch, n, out);
+        count_launch();
+    }
     GR_TRY_CUDA(c0, cudaGetLastError(), "compose");
     return GR_OK;
 }

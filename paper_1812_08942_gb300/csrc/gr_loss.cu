@@ -420,22 +420,28 @@ static gr_status loss_bwd_k(gr_ctx* cc, const float* saved, const float* w_c, in
     float* Nf = Qf + K;
     GR_TRY_CUDA(cc, cudaMemcpyAsync(Y, y0, sizeof(float) * nK, cudaMemcpyDeviceToDevice, s), "copy");
     k_param_degree<<<(unsigned)ceil_div(nc * 32, 256), 256, 0, s>>>(nc, cc->rowptr, cc->eid, w_c, D); count_launch();
-    for (int it = 0; it < S; ++it)
+    for (int it = 0; it < S; ++it) {
         k_param_sweep<K><<<(unsigned)ceil_div(nK, 256), 256, 0, s>>>(nc, cc->rowptr, cc->col, cc->eid, w_c, D,
                                                                      Y + it * nK, (float)omega, Z + it * nK,
-                                                                     Y + (it + 1) * nK); count_launch();
+                                                                     Y + (it + 1) * nK);
+        count_launch();
+    }
     k_sum_f32<<<1, 256, 0, s>>>(mass, nc, den); count_launch();  // total mass, FP64
     const float* yS = Y + (size_t)S * nK;
     GR_TRY_CUDA(cc, coarse_rc_parts<K>(cc, yS, w_c, mass, den, part, Nsum, musum, mu, Qsum), "rc");
     k_loss_scalars<<<1, 32, 0, s>>>(K, Nsum, Qsum, Rf, grad_loss, nullptr, gRc, Qf, Nf); count_launch();
     k_adj_final<K><<<(unsigned)ceil_div(nK, 256), 256, 0, s>>>(nc, cc->rowptr, cc->col, cc->eid, w_c, yS, mass,
                                                                mu, Qf, Nf, gRc, YB + (size_t)S * nK); count_launch();
-    for (int it = S - 1; it >= 0; --it)
+    for (int it = S - 1; it >= 0; --it) {
         k_param_sweep_adj<K><<<(unsigned)ceil_div(nK, 256), 256, 0, s>>>(
-            nc, cc->rowptr, cc->col, cc->eid, w_c, D, YB + (size_t)(it + 1) * nK, (float)omega, YB + (size_t)it * nK); count_launch();
-    if (cc->m > 0)
+            nc, cc->rowptr, cc->col, cc->eid, w_c, D, YB + (size_t)(it + 1) * nK, (float)omega, YB + (size_t)it * nK);
+        count_launch();
+    }
+    if (cc->m > 0) {
         k_edge_grad<K><<<(unsigned)ceil_div(cc->m, 256), 256, 0, s>>>(cc->m, cc->eu, cc->ev, S, nK, Y, Z, YB, D,
-                                                                      (float)omega, Qf, gRc, grad); count_launch();
+                                                                      (float)omega, Qf, gRc, grad);
+        count_launch();
+    }
     GR_TRY_CUDA(cc, cudaGetLastError(), "loss bwd");
     return GR_OK;
 }

@@ -352,8 +352,10 @@ static cudaError_t run_smooth(gr_ctx* c, int sweeps, double omega, uint64_t seed
     }
     if (ev1) GR_CUDA(cudaEventRecord(ev1, s));
     constexpr int G = RowLayout<T, K>::G;
-    if (n > 0)
-        k_apply<T, K><<<(unsigned)ceil_div(n * G, 256), 256, 0, s>>>(n, cur, X, sin); count_launch();
+    if (n > 0) {
+        k_apply<T, K><<<(unsigned)ceil_div(n * G, 256), 256, 0, s>>>(n, cur, X, sin);
+        count_launch();
+    }
     return cudaGetLastError();
 }
 
