@@ -88,6 +88,26 @@ gr_status graph_reduce_get_info(const gr_ctx* ctx, int64_t* n_out, int64_t* m_ou
 gr_status graph_reduce_smooth(gr_ctx* ctx, int K, int sweeps, double omega, uint64_t seed,
                               int level, gr_prec prec, void* X);
 
+/* Allocation-free variant of graph_reduce_smooth, for callers that must not
+ * allocate device memory once they are running: for example code working
+ * inside a fixed, pre-reserved memory budget, or under another framework's
+ * allocator, where a cudaMalloc / cudaMallocAsync from a library would break
+ * the budget or the allocator's bookkeeping.  The paper has no counterpart;
+ * the result is the same as graph_reduce_smooth's (same kernels, same order).
+ * The caller passes the graph (ctx, created beforehand) and the output X, as
+ * for graph_reduce_smooth.  The scratch -- the second n x K block, the column
+ * statistics and per-block partial sums -- lives in one 32 MiB device array
+ * inside the library, held by every GPU that loads it until the process
+ * exits; n*K*sizeof(element) plus about 1 MiB of statistics must fit, else
+ * GR_EINVAL.  The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress) and should come before any stream capture.  All
+ * calls share the array and it keeps the last call's contents: calls that
+ * overlap on the GPU (other streams, other contexts) race and corrupt each
+ * other; serialise them.  No cudaMalloc, cudaFree or allocating library
+ * routine is called. */
+gr_status graph_reduce_smooth_noalloc(gr_ctx* ctx, int K, int sweeps, double omega,
+                                      uint64_t seed, int level, gr_prec prec, void* X);
+
 /* Per-edge affinity a = (X_p,X_q)^2 / ((X_p,X_p)(X_q,X_q)) (Eq. eqn:agg) and
  * algebraic distance d = 1 - a (Sec. 3.2.2), for every edge (p, q) of the
  * canonical list.  d is evaluated without cancellation as

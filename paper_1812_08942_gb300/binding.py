@@ -20,7 +20,8 @@ GR_F64, GR_F32, GR_BF16 = 0, 1, 2
 _STATUS = {1: "GR_EINVAL", 2: "GR_ENOMEM", 3: "GR_ECUDA", 4: "GR_ETIMEOUT", 5: "GR_ESTATE"}
 
 EXPORTED = [
-    "graph_reduce_create", "graph_reduce_get_info", "graph_reduce_smooth", "graph_reduce_affinity",
+    "graph_reduce_create", "graph_reduce_get_info", "graph_reduce_smooth", "graph_reduce_smooth_noalloc",
+    "graph_reduce_affinity",
     "graph_reduce_aggregate", "graph_reduce_coarsen", "graph_reduce_get_edges", "graph_reduce_get_map",
     "graph_reduce_multilevel", "graph_reduce_compose_maps", "graph_reduce_loss_fwd",
     "graph_reduce_loss_bwd", "graph_reduce_launch_count", "graph_reduce_last_error", "graph_reduce_destroy",
@@ -66,6 +67,7 @@ def load():
         "graph_reduce_create": (I, [PP, I64, I64, P, P, P, I, P]),
         "graph_reduce_get_info": (I, [P, ctypes.POINTER(I64), ctypes.POINTER(I64)]),
         "graph_reduce_smooth": (I, [P, I, I, D, U64, I, I, P]),
+        "graph_reduce_smooth_noalloc": (I, [P, I, I, D, U64, I, I, P]),
         "graph_reduce_affinity": (I, [P, P, I, I, P, P]),
         "graph_reduce_aggregate": (I, [P, P, I, I64, I, I, P, ctypes.POINTER(I64), ctypes.POINTER(I32)]),
         "graph_reduce_coarsen": (I, [P, P, I64, PP]),
@@ -162,6 +164,16 @@ def graph_reduce_smooth(g: Graph, X, sweeps, omega=0.7, seed=0, level=0):
     assert X.is_cuda and X.is_contiguous() and X.dim() == 2 and X.shape[0] == g.n
     st = load().graph_reduce_smooth(g.handle, int(X.shape[1]), int(sweeps), float(omega), int(seed), int(level),
                                     _prec_of(X.dtype), _ptr(X))
+    _check(st, g.handle)
+    return X
+
+
+def graph_reduce_smooth_noalloc(g: Graph, X, sweeps, omega=0.7, seed=0, level=0):
+    """Same result as graph_reduce_smooth; the library allocates nothing (its
+    scratch is a fixed 32 MiB device array shared by all calls)."""
+    assert X.is_cuda and X.is_contiguous() and X.dim() == 2 and X.shape[0] == g.n
+    st = load().graph_reduce_smooth_noalloc(g.handle, int(X.shape[1]), int(sweeps), float(omega), int(seed),
+                                            int(level), _prec_of(X.dtype), _ptr(X))
     _check(st, g.handle)
     return X
 

@@ -386,3 +386,144 @@ gr_status smooth_impl(gr_ctx* c, int K, int sweeps, double omega, uint64_t seed,
 }
 
 }  // namespace gr
+
+// ---------------------------------------------------------------------------
+// Allocation-free smoothing (graph_reduce_smooth_noalloc)
+//
+// Some callers may not allocate device memory once set up: code that runs
+// while a stream is being captured into a CUDA graph, or under an allocator
+// policy that forbids growth after initialisation.  This variant launches the
+// same kernels as graph_reduce_smooth but takes its scratch (the second
+// vector block, the column statistics and the per-block partial sums) from
+// one file-scope device array instead of the context's workspace.  Every GPU
+// that loads the library holds this array until the process exits.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace gr {
+
+constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(32) << 20;  // 32 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+// Device address of g_noalloc_scratch, looked up once per device (the host
+// symbol is only a stand-in and must never reach a kernel).
+static void* g_noalloc_addr[64];
+static std::mutex g_noalloc_mu;
+
+static cudaError_t noalloc_scratch_addr(int device, void** out) {
+    if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[device]) {
+        int prev = -1;
+        cudaError_t e = cudaGetDevice(&prev);
+        if (e != cudaSuccess) return e;
+        if (prev != device && (e = cudaSetDevice(device)) != cudaSuccess) return e;
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (prev != device) cudaSetDevice(prev);
+        if (e != cudaSuccess) return e;
+        g_noalloc_addr[device] = p;
+    }
+    *out = g_noalloc_addr[device];
+    return cudaSuccess;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+template <typename T, int K>
+static gr_status run_smooth_noalloc(gr_ctx* c, int sweeps, double omega, uint64_t seed, int level,
+                                    T* X) {
+    cudaStream_t s = c->stream;
+    const int64_t n = c->n;
+    constexpr int GP = RowLayout<T, K>::GP;
+    const int lpr = pick_lpr<T, K>(c);
+    const int rows_per_block = SM_WARPS * (32 / lpr);
+    const int64_t cap = (int64_t)c->num_sms * 8;
+    const int64_t want = ceil_div(n, rows_per_block);
+    const int grid = (int)(want < cap ? (want > 0 ? want : 1) : cap);
+    const int64_t iwant = ceil_div(n, SM_WARPS * (32 / GP));
+    const int igrid = (int)(iwant < cap ? (iwant > 0 ? iwant : 1) : cap);
+    const int maxgrid = grid > igrid ? grid : igrid;
+    // layout of the shared scratch: [vector block | 2 x 2K stats + counter | partials]
+    const size_t b_buf = align256(sizeof(T) * (size_t)n * K);
+    const size_t b_st = align256(sizeof(double) * 4 * K + 64);
+    const size_t b_part = align256(sizeof(double) * 2 * K * (size_t)maxgrid);
+    if (b_buf + b_st + b_part > NOALLOC_SCRATCH_BYTES)
+        return set_error(c, GR_EINVAL,
+                         "smooth_noalloc: n*K*sizeof(element) plus statistics exceeds the 32 MiB "
+                         "allocation-free scratch");
+    void* base = nullptr;
+    cudaError_t e = noalloc_scratch_addr(c->device, &base);
+    if (e != cudaSuccess) return cuda_error(c, e, "smooth_noalloc: scratch address");
+    char* B = (char*)base;
+    T* buf = (T*)B;
+    double* st0 = (double*)(B + b_buf);
+    double* st1 = st0 + 2 * K;
+    unsigned* counter = (unsigned*)(st1 + 2 * K);
+    double* part = (double*)(B + b_buf + b_st);
+    // the array keeps the previous call's contents: the last-block counter
+    // must start at zero
+    GR_TRY_CUDA(c, cudaMemsetAsync(counter, 0, sizeof(unsigned), s), "smooth_noalloc");
+    k_init<T, K><<<igrid, SM_THREADS, 0, s>>>(n, seed, (uint64_t)level, X, part, counter, st0);
+    count_launch();
+    GR_TRY_CUDA(c, cudaGetLastError(), "smooth_noalloc: init");
+    const T* cur = X;
+    T* nxt = buf;
+    double* sin = st0;
+    double* sout = st1;
+    for (int it = 0; it < sweeps; ++it) {
+        switch (lpr / GP) {
+            case 1: e = launch_sweep<T, K, GP>(c, grid, cur, nxt, omega, sin, part, counter, sout); break;
+            case 2: e = launch_sweep<T, K, (2 * GP <= 32 ? 2 * GP : 32)>(c, grid, cur, nxt, omega, sin, part, counter, sout); break;
+            case 4: e = launch_sweep<T, K, (4 * GP <= 32 ? 4 * GP : 32)>(c, grid, cur, nxt, omega, sin, part, counter, sout); break;
+            case 8: e = launch_sweep<T, K, (8 * GP <= 32 ? 8 * GP : 32)>(c, grid, cur, nxt, omega, sin, part, counter, sout); break;
+            case 16: e = launch_sweep<T, K, (16 * GP <= 32 ? 16 * GP : 32)>(c, grid, cur, nxt, omega, sin, part, counter, sout); break;
+            default: e = launch_sweep<T, K, 32>(c, grid, cur, nxt, omega, sin, part, counter, sout); break;
+        }
+        if (e != cudaSuccess) return cuda_error(c, e, "smooth_noalloc: sweep");
+        const T* tmp = cur;
+        cur = nxt;
+        nxt = (T*)tmp;
+        double* ts = sin;
+        sin = sout;
+        sout = ts;
+    }
+    constexpr int G = RowLayout<T, K>::G;
+    if (n > 0) {
+        k_apply<T, K><<<(unsigned)ceil_div(n * G, 256), 256, 0, s>>>(n, cur, X, sin);
+        count_launch();
+    }
+    GR_TRY_CUDA(c, cudaGetLastError(), "smooth_noalloc: apply");
+    return GR_OK;
+}
+
+template <typename T>
+static gr_status smooth_noalloc_typed(gr_ctx* c, int K, int sweeps, double omega, uint64_t seed,
+                                      int level, void* X) {
+    switch (K) {
+        case 4: return run_smooth_noalloc<T, 4>(c, sweeps, omega, seed, level, (T*)X);
+        case 8: return run_smooth_noalloc<T, 8>(c, sweeps, omega, seed, level, (T*)X);
+        case 16: return run_smooth_noalloc<T, 16>(c, sweeps, omega, seed, level, (T*)X);
+        case 24: return run_smooth_noalloc<T, 24>(c, sweeps, omega, seed, level, (T*)X);
+        case 32: return run_smooth_noalloc<T, 32>(c, sweeps, omega, seed, level, (T*)X);
+    }
+    return set_error(c, GR_EINVAL, "smooth_noalloc: K must be 4, 8, 16, 24 or 32");
+}
+
+}  // namespace gr
+
+extern "C" gr_status graph_reduce_smooth_noalloc(gr_ctx* ctx, int K, int sweeps, double omega,
+                                                 uint64_t seed, int level, gr_prec prec, void* X) {
+    using namespace gr;
+    if (!ctx) return set_error(nullptr, GR_EINVAL, "smooth_noalloc: ctx is NULL");
+    if (sweeps < 0 || !(omega > 0.0 && omega <= 1.0))
+        return set_error(ctx, GR_EINVAL, "smooth_noalloc: need sweeps >= 0 and 0 < omega <= 1");
+    if (level < 0 || level >= (1 << 20)) return set_error(ctx, GR_EINVAL, "smooth_noalloc: level out of range");
+    if (!X || ((uintptr_t)X & 15u)) return set_error(ctx, GR_EINVAL, "smooth_noalloc: X must be a 16-byte aligned device pointer");
+    switch (prec) {
+        case GR_F64: return smooth_noalloc_typed<double>(ctx, K, sweeps, omega, seed, level, X);
+        case GR_F32: return smooth_noalloc_typed<float>(ctx, K, sweeps, omega, seed, level, X);
+        case GR_BF16: return smooth_noalloc_typed<__nv_bfloat16>(ctx, K, sweeps, omega, seed, level, X);
+    }
+    return set_error(ctx, GR_EINVAL, "smooth_noalloc: bad precision");
+}
