@@ -31,7 +31,7 @@ if ROOT not in sys.path:
 
 METRIC = "input edges/s per aggregation level (sum over levels of m_l / step time)"
 UNIT = "edges/s"
-DEFAULT_WORKLOAD = "chunglu_434k"
+DEFAULT_WORKLOAD = "mesh3d_128"
 # bounded oracle sample: the same Chung-Lu recipe at 1/8 scale
 SAMPLE_DIV = 8
 
@@ -45,6 +45,7 @@ def parse_args():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 pipeline comparison")
     return ap.parse_args()
 
 
@@ -161,7 +162,7 @@ def oracle_sample_graph(workload):
             SAMPLE_DIV, g.n, g.m)
     elif workload == "mesh3d_128":
         g = W.mesh3d(64, 64, 64)
-        desc = "64^3 7-point mesh, log-normal weights (1/8 of the nodes)"
+        desc = "64^3 7-point mesh, log-normal weights (the same recipe at 1/8 of the nodes)"
     elif workload == "grid2d_64":
         g = W.grid2d(64, 64)
         desc = "the full 64x64 grid"
@@ -352,6 +353,49 @@ def main():
         e2e = {"value": edges_per_step * k_e2e * world / te, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "steps": k_e2e}
 
+    # FP32 (or BF16) path against the plain FP64 GPU path on the same graph:
+    # step-time speedup, and the 10 smallest nontrivial eigenvalues of the two
+    # final reduced graphs (FP64 solver on the host)
+    cmp64 = None
+    if rank == 0 and world == 1 and not args.no_fp64 and prec != gr.GR_F64:
+        p64 = gr.ReduceParams(K=wl.K, sweeps=wl.sweeps, omega=wl.omega, seed=0, prec=gr.GR_F64, passes=2,
+                              level_ratio=4, final_target=wl.final_target, max_levels=32)
+
+        def step64():
+            G = gr.graph_reduce_create(g.n, u_d, v_d, w_d)
+            levels, _ = gr.graph_reduce_multilevel(G, p64, want_stats=False)
+            return G, levels
+
+        G64, lv64 = step64()  # warm-up (FP64 slot packing, scratch)
+        del G64, lv64
+        k64 = max(1, min(args.steps, 3))
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(k64):
+            G64, lv64 = step64()
+            if _ < k64 - 1:
+                del G64, lv64
+        e1.record()
+        torch.cuda.synchronize()
+        t64 = e0.elapsed_time(e1) / k64
+        import oracle as _or  # host FP64 eigen solver only
+        G32 = gr.graph_reduce_create(g.n, u_d, v_d, w_d)
+        lv32, _ = gr.graph_reduce_multilevel(G32, params, want_stats=False)
+        ev = []
+        for lv in (lv32, lv64):
+            fu, fv, fw = (t.numpy() for t in gr.graph_reduce_get_edges(lv[-1], on_host=True))
+            ev.append(_or.smallest_nontrivial_eigs(lv[-1].n, fu, fv, fw, 10))
+        rel = float(np.max(np.abs(ev[0] - ev[1]) / np.abs(ev[1])))
+        same_maps = all(torch.equal(gr.graph_reduce_get_map(a), gr.graph_reduce_get_map(b))
+                        for a, b in zip(lv32, lv64)) and len(lv32) == len(lv64)
+        cmp64 = {"ms_per_step_fp64": t64, "ms_per_step": t_max / args.steps,
+                 "speedup": t64 / (t_max / args.steps), "lambda10_max_rel_err": rel,
+                 "at_accuracy": bool(rel <= 1e-3), "aggregates_identical": bool(same_maps),
+                 "lambda10_fp64": [float(x) for x in ev[1]]}
+        del G32, lv32, G64, lv64
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         gs, desc = oracle_sample_graph(args.workload)
@@ -371,6 +415,7 @@ def main():
                        "l2": "inputs larger than L2 (edge list %.0f MB + CSR %.0f MB vs 129 MB); no flush"
                              % (g.m * 16 / 1e6, g.m * 2 * 24 / 1e6)},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "fp32_vs_fp64": cmp64,
             "clocks": clocks, "levels": per_level,
         }
         print(json.dumps(line), flush=True)

@@ -58,7 +58,12 @@ struct AggState {
     int32_t* keep;     // per pair
     int32_t* flags;    // n: label scan input
     int32_t* lab;      // n
-    int32_t* ctr;      // [0],[1] worklist counts, [2] pair count, [3] error flag
+    uint64_t* tk_hi;   // n * TOPK cached candidate keys
+    uint32_t* tk_lo;   // n * TOPK
+    int32_t* tk_nb;    // n * TOPK cached candidate clusters
+    uint8_t* tk_cnt;   // n: number of cached candidates
+    uint64_t* keys;    // 2m per-slot keys (FP32 distances), else unused
+    int32_t* ctr;      // [0],[1] worklist counts, [2] pair count, [3] [4] error flags
 };
 
 __global__ void k_agg_init(int64_t n, int32_t* __restrict__ cl, int32_t* __restrict__ nxt,
@@ -70,6 +75,21 @@ __global__ void k_agg_init(int64_t n, int32_t* __restrict__ cl, int32_t* __restr
     tail[i] = (int32_t)i;
 }
 
+// Append `item` to a worklist when `keep`: one atomic per warp, entries of a
+// warp stay contiguous and in lane order (keeps neighbouring rows together).
+__device__ __forceinline__ void warp_append(bool keep, int32_t item, int32_t* __restrict__ list,
+                                            int32_t* __restrict__ count) {
+    const unsigned active = __activemask();
+    const unsigned ball = __ballot_sync(active, keep);
+    if (!ball) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(ball) - 1;
+    int32_t base = 0;
+    if (lane == leader) base = atomicAdd(count, __popc(ball));
+    base = __shfl_sync(active, base, leader);
+    if (keep) list[base + __popc(ball & ((1u << lane) - 1u))] = item;
+}
+
 // start of a pass: every cluster head becomes free and joins the worklist
 __global__ void k_pass_init(int64_t n, const int32_t* __restrict__ cl, uint8_t* __restrict__ status,
                             int32_t* __restrict__ best, int32_t* __restrict__ wl,
@@ -78,66 +98,156 @@ __global__ void k_pass_init(int64_t n, const int32_t* __restrict__ cl, uint8_t* 
     if (i >= n) return;
     best[i] = -1;
     status[i] = ST_FREE;
-    if (cl[i] == (int32_t)i) {
-        int32_t pos = atomicAdd(&ctr[0], 1);
-        wl[pos] = (int32_t)i;
-    }
+    warp_append(cl[i] == (int32_t)i, (int32_t)i, wl, &ctr[0]);
+}
+
+// Per-slot keys for FP32 distances: (float bits << 32 | edge id) of the slot's
+// edge, so every round reads one coalesced 8-byte key per slot.
+__global__ void k_slot_keys(int64_t slots, const int32_t* __restrict__ eid, const float* __restrict__ d,
+                            uint64_t* __restrict__ keys, int32_t* __restrict__ err) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= slots) return;
+    const int32_t e = eid[j];
+    const float x = __ldg(d + e);
+    if (!(x >= 0.f)) atomicExch(err, 1);
+    const uint64_t b = x == 0.f ? 0ull : (uint64_t)(uint32_t)__float_as_int(x);
+    keys[j] = (b << 32) | (uint64_t)(uint32_t)e;
+}
+
+constexpr int TOPK = 1;  // cached candidates per cluster (1 measured best: deeper caches cost more than the rescans they save)
+
+__device__ __forceinline__ Key key_inf() {
+    Key k;
+    k.hi = ~0ull;
+    k.lo = ~0u;
+    return k;
 }
 
 // Each free cluster finds its smallest key towards another free cluster.
-// LPC lanes per cluster walk the members' CSR rows.
-template <bool D64, int LPC>
+// LPC lanes per cluster walk the members' CSR rows and keep the TOPK smallest
+// candidates (neighbours only ever leave the free set, so the first cached
+// candidate that is still free is the current best; a cluster rescans only
+// when all TOPK cached candidates are gone).  In the first pass every node is
+// its own cluster, so the cluster-id gather is skipped; in the first round of
+// a pass every cluster is free, so the status gather is skipped too.
+template <bool D64, int LPC, bool FIRST_PASS>
 __global__ void k_propose(const int32_t* __restrict__ wl, const int32_t* __restrict__ wl_count,
                           int32_t* __restrict__ next_count, const int64_t* __restrict__ rowptr,
                           const int32_t* __restrict__ col, const int32_t* __restrict__ eid,
-                          const void* __restrict__ d, const int32_t* __restrict__ cl,
-                          const int32_t* __restrict__ nxt, uint8_t* __restrict__ status,
-                          int32_t* __restrict__ best, uint64_t* __restrict__ bhi,
-                          uint32_t* __restrict__ blo, int32_t* __restrict__ err) {
+                          const uint64_t* __restrict__ keys, const void* __restrict__ d,
+                          const int32_t* __restrict__ cl, const int32_t* __restrict__ nxt,
+                          uint8_t* __restrict__ status, int32_t* __restrict__ best, uint64_t* __restrict__ bhi,
+                          uint32_t* __restrict__ blo, uint64_t* __restrict__ tk_hi, uint32_t* __restrict__ tk_lo,
+                          int32_t* __restrict__ tk_nb, uint8_t* __restrict__ tk_cnt, int first_round,
+                          int32_t* __restrict__ err) {
     if (blockIdx.x == 0 && threadIdx.x == 0) *next_count = 0;
     const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / LPC;
     const int l = threadIdx.x % LPC;
     const int count = *wl_count;
     if (g >= count) return;
-    const int32_t c = wl[g];
-    const int32_t b0 = best[c];
-    if (b0 >= 0 && status[b0] == ST_FREE) return;  // previous best still free: still the best
     const unsigned gmask = LPC == 32 ? 0xffffffffu : (((1u << LPC) - 1u) << ((threadIdx.x & 31) / LPC * LPC));
-    Key bk;
-    bk.hi = ~0ull;
-    bk.lo = ~0u;
-    int32_t bn = -1;
-    for (int32_t p = c; p >= 0; p = nxt[p]) {
+    const int gbase_lane = (threadIdx.x & 31) / LPC * LPC;
+    const int32_t c = wl[g];
+    // 1) cached candidates
+    const int cnt = first_round ? 0 : tk_cnt[c];
+    if (cnt > 0) {
+        bool fr = false;
+        if (l < cnt) fr = status[tk_nb[(int64_t)c * TOPK + l]] == ST_FREE;
+        const unsigned ball = __ballot_sync(gmask, fr) >> gbase_lane;
+        if (ball) {
+            const int f = __ffs(ball) - 1;
+            if (l == 0) {
+                best[c] = tk_nb[(int64_t)c * TOPK + f];
+                bhi[c] = tk_hi[(int64_t)c * TOPK + f];
+                blo[c] = tk_lo[(int64_t)c * TOPK + f];
+            }
+            return;
+        }
+        if (cnt < TOPK) {  // every free neighbour the scan saw is gone
+            if (l == 0) status[c] = ST_DEAD;
+            return;
+        }
+    }
+    // 2) scan: per-lane sorted lists of the TOPK smallest candidates
+    Key lk[TOPK];
+    int32_t ln[TOPK];
+#pragma unroll
+    for (int t = 0; t < TOPK; ++t) {
+        lk[t] = key_inf();
+        ln[t] = -1;
+    }
+    for (int32_t p = c; p >= 0; p = FIRST_PASS ? -1 : nxt[p]) {
         const int64_t e_end = rowptr[p + 1];
         for (int64_t j = rowptr[p] + l; j < e_end; j += LPC) {
-            const int32_t cq = cl[col[j]];
-            if (cq == c || status[cq] != ST_FREE) continue;
-            Key k = make_key<D64>(d, eid[j], err);
-            if (key_less(k, bk)) {
-                bk = k;
-                bn = cq;
+            const int32_t cq = FIRST_PASS ? col[j] : cl[col[j]];
+            if (!FIRST_PASS && cq == c) continue;
+            if (!first_round && status[cq] != ST_FREE) continue;
+            Key k;
+            if constexpr (D64) {
+                k = make_key<true>(d, eid[j], err);
+            } else {
+                k.hi = keys[j];
+                k.lo = 0u;
+            }
+            if (key_less(k, lk[TOPK - 1])) {
+                lk[TOPK - 1] = k;
+                ln[TOPK - 1] = cq;
+#pragma unroll
+                for (int t = TOPK - 1; t > 0; --t)
+                    if (key_less(lk[t], lk[t - 1])) {
+                        Key tk = lk[t];
+                        lk[t] = lk[t - 1];
+                        lk[t - 1] = tk;
+                        int32_t tn = ln[t];
+                        ln[t] = ln[t - 1];
+                        ln[t - 1] = tn;
+                    }
             }
         }
     }
+    // 3) merge the lanes' lists: TOPK rounds of group argmin over list heads
+    int found = 0;
 #pragma unroll
-    for (int o = LPC / 2; o > 0; o >>= 1) {
-        Key ok;
-        ok.hi = __shfl_xor_sync(gmask, bk.hi, o, LPC);
-        ok.lo = __shfl_xor_sync(gmask, bk.lo, o, LPC);
-        int32_t on = __shfl_xor_sync(gmask, bn, o, LPC);
-        if (key_less(ok, bk)) {
-            bk = ok;
-            bn = on;
+    for (int t = 0; t < TOPK; ++t) {
+        Key bk = lk[0];
+        int bl = l;
+#pragma unroll
+        for (int o = LPC / 2; o > 0; o >>= 1) {
+            Key ok;
+            ok.hi = __shfl_xor_sync(gmask, bk.hi, o, LPC);
+            ok.lo = __shfl_xor_sync(gmask, bk.lo, o, LPC);
+            const int ol = __shfl_xor_sync(gmask, bl, o, LPC);
+            if (key_less(ok, bk) || (ok.hi == bk.hi && ok.lo == bk.lo && ol < bl)) {
+                bk = ok;
+                bl = ol;
+            }
         }
+        const int32_t bnb = __shfl_sync(gmask, ln[0], bl, LPC);
+        if (bk.hi == ~0ull && bk.lo == ~0u) break;  // uniform across the group
+        if (l == 0) {
+            tk_hi[(int64_t)c * TOPK + t] = bk.hi;
+            tk_lo[(int64_t)c * TOPK + t] = bk.lo;
+            tk_nb[(int64_t)c * TOPK + t] = bnb;
+            if (t == 0) {
+                best[c] = bnb;
+                bhi[c] = bk.hi;
+                blo[c] = bk.lo;
+            }
+        }
+        if (l == bl) {  // pop the winner's head
+#pragma unroll
+            for (int u = 0; u < TOPK - 1; ++u) {
+                lk[u] = lk[u + 1];
+                ln[u] = ln[u + 1];
+            }
+            lk[TOPK - 1] = key_inf();
+            ln[TOPK - 1] = -1;
+        }
+        ++found;
     }
     if (l == 0) {
-        if (bn < 0) {
-            status[c] = ST_DEAD;  // no free neighbour now, none later in this pass
-        } else {
-            best[c] = bn;
-            bhi[c] = bk.hi;
-            blo[c] = bk.lo;
-        }
+        tk_cnt[c] = (uint8_t)found;
+        if (found == 0) status[c] = ST_DEAD;  // no free neighbour now, none later in this pass
     }
 }
 
@@ -154,7 +264,8 @@ __global__ void k_accept(const int32_t* __restrict__ wl, const int32_t* __restri
     const int32_t c = wl[i];
     if (status[c] != ST_FREE) return;  // dead this round
     const int32_t b = best[c];
-    if (best[b] == c) {
+    const bool matched = best[b] == c;
+    if (matched) {
         status[c] = ST_MATCHED;
         if (c < b) {
             int32_t k = atomicAdd(npairs, 1);
@@ -163,10 +274,8 @@ __global__ void k_accept(const int32_t* __restrict__ wl, const int32_t* __restri
             phi[k] = bhi[c];
             plo[k] = blo[c];
         }
-    } else {
-        int32_t pos = atomicAdd(next_count, 1);
-        wl_next[pos] = c;
     }
+    warp_append(!matched, c, wl_next, next_count);
 }
 
 __global__ void k_pairs_keys(int32_t npairs, const uint64_t* __restrict__ phi,
@@ -222,13 +331,20 @@ __global__ void k_gather_u64(const uint64_t* __restrict__ src, const uint32_t* _
     if (i < count) out[i] = src[idx[i]];
 }
 
-template <bool D64, int LPC>
+template <bool D64, int LPC, bool FIRST_PASS>
 static void launch_propose(gr_ctx* c, AggState& S, int r, int64_t bound, const void* d) {
     const int64_t threads = bound * LPC;
     const unsigned grid = (unsigned)(threads > 0 ? ceil_div(threads, 256) : 1);
-    k_propose<D64, LPC><<<grid, 256, 0, c->stream>>>(S.wl[r & 1], S.ctr + (r & 1), S.ctr + ((r + 1) & 1),
-                                                      c->rowptr, c->col, c->eid, d, S.cl, S.nxt,
-                                                      S.status, S.best, S.bhi, S.blo, S.ctr + 3); count_launch();
+    k_propose<D64, LPC, FIRST_PASS><<<grid, 256, 0, c->stream>>>(
+        S.wl[r & 1], S.ctr + (r & 1), S.ctr + ((r + 1) & 1), c->rowptr, c->col, c->eid, S.keys, d, S.cl, S.nxt,
+        S.status, S.best, S.bhi, S.blo, S.tk_hi, S.tk_lo, S.tk_nb, S.tk_cnt, r == 0 ? 1 : 0, S.ctr + 3);
+    count_launch();
+}
+
+template <bool D64, int LPC>
+static void launch_propose_pass(gr_ctx* c, AggState& S, int r, int64_t bound, const void* d, bool first_pass) {
+    if (first_pass) launch_propose<D64, LPC, true>(c, S, r, bound, d);
+    else launch_propose<D64, LPC, false>(c, S, r, bound, d);
 }
 
 gr_status aggregate_impl(gr_ctx* c, const void* d, int d_is_f64, int64_t target_nc, int passes,
@@ -247,7 +363,8 @@ gr_status aggregate_impl(gr_ctx* c, const void* d, int d_is_f64, int64_t target_
                  o_best = add(4 * n), o_bhi = add(8 * n), o_blo = add(4 * n), o_wl0 = add(4 * n),
                  o_wl1 = add(4 * n), o_pc = add(4 * n), o_pb = add(4 * n), o_phi = add(8 * n),
                  o_plo = add(4 * n), o_keep = add(4 * n), o_flags = add(4 * n), o_lab = add(4 * n),
-                 o_ctr = add(64);
+                 o_tkhi = add(8 * TOPK * n), o_tklo = add(4 * TOPK * n), o_tknb = add(4 * TOPK * n),
+                 o_tkcnt = add(n), o_keys = add(d_is_f64 ? 8 : 8 * 2 * c->m), o_ctr = add(64);
     void* base;
     GR_TRY_CUDA(c, c->ws.get(WS_AGG_STATE, need, &base), "aggregate scratch");
     char* B = (char*)base;
@@ -268,6 +385,11 @@ gr_status aggregate_impl(gr_ctx* c, const void* d, int d_is_f64, int64_t target_
     S.keep = (int32_t*)(B + o_keep);
     S.flags = (int32_t*)(B + o_flags);
     S.lab = (int32_t*)(B + o_lab);
+    S.tk_hi = (uint64_t*)(B + o_tkhi);
+    S.tk_lo = (uint32_t*)(B + o_tklo);
+    S.tk_nb = (int32_t*)(B + o_tknb);
+    S.tk_cnt = (uint8_t*)(B + o_tkcnt);
+    S.keys = (uint64_t*)(B + o_keys);
     S.ctr = (int32_t*)(B + o_ctr);
     int64_t* hs = host_scratch();
     if (!hs) return set_error(c, GR_ENOMEM, "aggregate: pinned scratch unavailable");
@@ -276,6 +398,11 @@ gr_status aggregate_impl(gr_ctx* c, const void* d, int d_is_f64, int64_t target_
     const unsigned gn = (unsigned)ceil_div(n > 0 ? n : 1, 256);
     k_agg_init<<<gn, 256, 0, s>>>(n, S.cl, S.nxt, S.tail); count_launch();
     GR_TRY_CUDA(c, cudaMemsetAsync(S.ctr, 0, 64, s), "memset");
+    if (!d_is_f64 && c->m > 0) {
+        k_slot_keys<<<(unsigned)ceil_div(2 * c->m, 256), 256, 0, s>>>(2 * c->m, c->eid, (const float*)d, S.keys,
+                                                                       S.ctr + 4);
+        count_launch();
+    }
     const double avg = n > 0 ? 2.0 * (double)c->m / (double)n : 0.0;
     const int lpc = avg >= 24 ? 32 : (avg >= 6 ? 8 : 4);
 
@@ -291,23 +418,24 @@ gr_status aggregate_impl(gr_ctx* c, const void* d, int d_is_f64, int64_t target_
         while (nlive > 0) {
             const int batch = r < 2 ? 1 : 4;
             for (int bi = 0; bi < batch; ++bi, ++r) {
+                const bool fp = pass == 0;
                 if (d_is_f64) {
-                    if (lpc == 32) launch_propose<true, 32>(c, S, r, nlive, d);
-                    else if (lpc == 8) launch_propose<true, 8>(c, S, r, nlive, d);
-                    else launch_propose<true, 4>(c, S, r, nlive, d);
+                    if (lpc == 32) launch_propose_pass<true, 32>(c, S, r, nlive, d, fp);
+                    else if (lpc == 8) launch_propose_pass<true, 8>(c, S, r, nlive, d, fp);
+                    else launch_propose_pass<true, 4>(c, S, r, nlive, d, fp);
                 } else {
-                    if (lpc == 32) launch_propose<false, 32>(c, S, r, nlive, d);
-                    else if (lpc == 8) launch_propose<false, 8>(c, S, r, nlive, d);
-                    else launch_propose<false, 4>(c, S, r, nlive, d);
+                    if (lpc == 32) launch_propose_pass<false, 32>(c, S, r, nlive, d, fp);
+                    else if (lpc == 8) launch_propose_pass<false, 8>(c, S, r, nlive, d, fp);
+                    else launch_propose_pass<false, 4>(c, S, r, nlive, d, fp);
                 }
                 k_accept<<<(unsigned)ceil_div(nlive, 256), 256, 0, s>>>(
                     S.wl[r & 1], S.ctr + (r & 1), S.wl[(r + 1) & 1], S.ctr + ((r + 1) & 1), S.status,
                     S.best, S.bhi, S.blo, S.pc, S.pb, S.phi, S.plo, S.ctr + 2); count_launch();
             }
             GR_TRY_CUDA(c, cudaGetLastError(), "aggregate rounds");
-            GR_TRY_CUDA(c, cudaMemcpyAsync(hctr, S.ctr, 16, cudaMemcpyDeviceToHost, s), "readback");
+            GR_TRY_CUDA(c, cudaMemcpyAsync(hctr, S.ctr, 32, cudaMemcpyDeviceToHost, s), "readback");
             GR_TRY_CUDA(c, cudaStreamSynchronize(s), "sync");
-            if (hctr[3]) return set_error(c, GR_EINVAL, "aggregate: distances must be >= 0 and not NaN");
+            if (hctr[3] || hctr[4]) return set_error(c, GR_EINVAL, "aggregate: distances must be >= 0 and not NaN");
             const int64_t prev = nlive;
             nlive = hctr[r & 1];
             // every round removes at least the pair across the smallest free-free key

@@ -319,7 +319,7 @@ void graph_reduce_destroy(gr_ctx* c) {
     if (!c) return;
     cudaStream_t s = c->stream;
     void* ptrs[] = {c->eu, c->ev, c->ew, c->eptr, c->rowptr, c->col, c->eid, c->cw32, c->wn64, c->deg,
-                    c->parent_map};
+                    c->parent_map, c->wpart, c->cw64};
     for (void* p : ptrs)
         if (p) cudaFreeAsync(p, s);
     c->ws.release();

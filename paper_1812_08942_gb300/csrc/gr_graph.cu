@@ -100,6 +100,25 @@ __global__ void k_degree_scale(const int64_t* __restrict__ rowptr, const int32_t
     }
 }
 
+// thread per row (short rows): D(p,p) summed sequentially in slot order,
+// which is ascending edge id -- the plain definition's order
+__global__ void k_degree_scale_rows(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                    int64_t n, double* __restrict__ wn64, int2* __restrict__ cw32,
+                                    double* __restrict__ deg) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int64_t b = rowptr[p], e = rowptr[p + 1];
+    double s = 0.0;
+    for (int64_t j = b; j < e; ++j) s += wn64[j];
+    deg[p] = s;
+    const double inv = s > 0.0 ? 1.0 / s : 0.0;
+    for (int64_t j = b; j < e; ++j) {
+        const double x = wn64[j] * inv;
+        wn64[j] = x;
+        cw32[j] = make_int2(col[j], __float_as_int((float)x));
+    }
+}
+
 gr_status build_csr(gr_ctx* c) {
     const int64_t n = c->n, m = c->m;
     cudaStream_t s = c->stream;
@@ -151,8 +170,13 @@ gr_status build_csr(gr_ctx* c) {
                                                               c->rowptr, c->col, c->eid, c->wn64); count_launch();
     }
     if (n > 0) {
-        k_degree_scale<<<(unsigned)ceil_div(n * 32, TB), TB, 0, s>>>(c->rowptr, c->col, n, c->wn64,
-                                                                    c->cw32, c->deg);
+        if (2 * m < 32 * n) {  // mean degree below 32: a thread per row
+            k_degree_scale_rows<<<(unsigned)ceil_div(n, TB), TB, 0, s>>>(c->rowptr, c->col, n, c->wn64, c->cw32,
+                                                                         c->deg);
+        } else {
+            k_degree_scale<<<(unsigned)ceil_div(n * 32, TB), TB, 0, s>>>(c->rowptr, c->col, n, c->wn64, c->cw32,
+                                                                        c->deg);
+        }
         count_launch();
     }
     GR_TRY_CUDA(c, cudaGetLastError(), "csr kernels");

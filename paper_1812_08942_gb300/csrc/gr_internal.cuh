@@ -67,6 +67,10 @@ struct gr_ctx {
     int2* cw32 = nullptr;       // 2m: (col, float bits of w / deg_row)
     double* wn64 = nullptr;     // 2m: w / deg_row
     double* deg = nullptr;      // n
+    // slot-balanced row partition for the streaming sweep (W+1 row starts)
+    int32_t* wpart = nullptr;
+    int64_t wpart_W = 0;
+    int4* cw64 = nullptr;       // 2m: (col, 0, w / deg_row as FP64), built on first FP64 sweep
     // mapping from the parent level (coarse contexts only)
     int32_t* parent_map = nullptr;
     int64_t parent_n = 0;

@@ -256,6 +256,303 @@ __global__ void __launch_bounds__(SM_THREADS) k_sweep(
     block_stats<Acc, K, E, G, LPR>(s1, s2, part, counter, n, stats_out);
 }
 
+// ---------------------------------------------------------------------------
+// Streaming sweep.
+//
+// Each warp owns a contiguous row range holding about the same number of
+// slots (+ ST_ROW_COST per row), so its slot list is one contiguous stream.
+// The warp keeps ST_D batches of 32 slots in flight into a private shared-
+// memory ring with cp.async (16 B per lane, L2 only), so the DRAM latency of
+// the slot stream overlaps the L2 gathers of the neighbour rows.
+// The warp takes one row at a time, 32 slots per step (LPR = 32): GP lanes
+// own a 16-byte chunk of the vector row and TS = 32 / GP neighbours are
+// gathered per round.
+// Slots: (column, FP32 weight) for FP32 / BF16 blocks, (column, pad, FP64
+// weight) for FP64 blocks.
+// ---------------------------------------------------------------------------
+constexpr int ST_NB = 16;              // ring batches per warp
+constexpr int ST_D = 8;                // batches kept in flight ahead of use
+constexpr int ST_RING = ST_NB * 32;    // ring slots per warp
+constexpr int ST_SPAN = ST_NB - ST_D;  // batches one window may span
+constexpr int ST_ROW_COST = 8;         // partition weight of a row, in slots
+
+template <typename T>
+struct SlotOf { using type = int2; };
+template <>
+struct SlotOf<double> { using type = int4; };
+__device__ __forceinline__ int slot_col(const int2& v) { return v.x; }
+__device__ __forceinline__ int slot_col(const int4& v) { return v.x; }
+__device__ __forceinline__ float slot_w(const int2& v, float) { return __int_as_float(v.y); }
+__device__ __forceinline__ double slot_w(const int4& v, double) { return __hiloint2double(v.w, v.z); }
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// wpart[w] = first row r with rowptr[r] + ST_ROW_COST * r >= w * C / W
+__global__ void k_warp_partition(int64_t n, const int64_t* __restrict__ rowptr, int64_t W,
+                                 int32_t* __restrict__ wpart) {
+    int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (w > W) return;
+    const double C = (double)rowptr[n] + (double)ST_ROW_COST * (double)n;
+    const double target = C * (double)w / (double)W;
+    int64_t lo = 0, hi = n;  // answer in [0, n]
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if ((double)rowptr[mid] + (double)ST_ROW_COST * (double)mid >= target) hi = mid;
+        else lo = mid + 1;
+    }
+    wpart[w] = (int32_t)(w == W ? n : lo);
+}
+
+// (col, 0, w) packed slots for the FP64 stream
+__global__ void k_pack64(int64_t slots, const int32_t* __restrict__ col, const double* __restrict__ wn64,
+                         int4* __restrict__ cw64) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < slots) {
+        double w = wn64[j];
+        cw64[j] = make_int4(col[j], 0, __double2loint(w), __double2hiint(w));
+    }
+}
+
+template <typename T, int K, int LPR>
+__global__ void __launch_bounds__(SM_THREADS) k_sweep_stream(
+    int64_t n, const int64_t* __restrict__ rowptr, const typename SlotOf<T>::type* __restrict__ slots,
+    int64_t total_slots, const int32_t* __restrict__ wpart, const T* __restrict__ Ain, T* __restrict__ Aout,
+    double omega_d, const double* __restrict__ stats_in, double* __restrict__ part,
+    unsigned* __restrict__ counter, double* __restrict__ stats_out) {
+    using Slot = typename SlotOf<T>::type;
+    using L = RowLayout<T, K>;
+    using Acc = typename AccOf<T>::type;
+    constexpr int E = L::E, G = L::G, GP = L::GP;
+    static_assert(LPR == 32, "one row per warp");
+    constexpr int TS = 32 / GP;                  // neighbours per round
+    constexpr int PER_LANE = 16 / (int)sizeof(Slot);  // slots one 16-byte copy moves
+    constexpr int COPY_LANES = 32 / PER_LANE;
+    extern __shared__ __align__(16) unsigned char st_dyn[];
+    __shared__ Acc st_sh[2 * K];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int q = lane % GP, t = lane / GP;
+    const bool chunk_ok = q < G;
+    const Acc omega = (Acc)omega_d, one_m = (Acc)(1.0 - omega_d);
+    for (int i = threadIdx.x; i < 2 * K; i += blockDim.x) st_sh[i] = (Acc)stats_in[i];
+    __syncthreads();
+    Slot* ring = reinterpret_cast<Slot*>(st_dyn) + warp * ST_RING;
+    Acc s1[E], s2[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) s1[e] = s2[e] = Acc(0);
+
+    const int64_t wg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int32_t r0 = wpart[wg], r1 = wpart[wg + 1];
+    if (r0 < r1) {
+        // stream positions are 32-bit offsets from B0 (a warp's range is < 2^31 slots)
+        const int64_t S0 = rowptr[r0];
+        const int64_t B0 = S0 & ~(int64_t)31;
+        const int32_t o_s0 = (int32_t)(S0 - B0);
+        const int32_t o_s1 = (int32_t)(rowptr[r1] - B0);
+        const int32_t o_tot = (int32_t)((total_slots - B0) < 0x7fffffff ? (total_slots - B0) : 0x7fffffff);
+        const Slot* src = slots + B0;
+        // batch k: offsets [32k, 32k + 32); COPY_LANES lanes move 16 bytes each
+        auto issue = [&](int32_t k) {
+            const int32_t o = 32 * k + PER_LANE * lane;
+            if (lane < COPY_LANES && o < o_s1 && o + PER_LANE > o_s0 && o < o_tot)
+                cp_async16(&ring[o & (ST_RING - 1)], src + o);
+            cp_async_commit();
+        };
+#pragma unroll 1
+        for (int k = 0; k < ST_D; ++k) issue(k);
+        int32_t ready = 0;  // batches [0, ready) have landed
+        // the window [lo, hi] of batches must fit the ring: hi - lo < ST_SPAN
+        auto ensure = [&](int32_t kb_hi) {
+            while (ready <= kb_hi) {
+                cp_async_wait<ST_D - 1>();
+                __syncwarp();
+                issue(ready + ST_D);
+                ++ready;
+            }
+        };
+        int32_t rp_base = r0;  // lane l caches rowptr[rp_base + 1 + l] - B0
+        int32_t rp_next = (r0 + 1 + lane <= n) ? (int32_t)(rowptr[r0 + 1 + lane] - B0) : 0;
+        int32_t gb = o_s0;     // start of the current row
+        {
+            for (int32_t row = r0; row < r1; ++row) {
+                if (row - rp_base >= 32) {
+                    rp_base = row;
+                    rp_next = (row + 1 + lane <= n) ? (int32_t)(rowptr[row + 1 + lane] - B0) : 0;
+                }
+                const int32_t e_end = __shfl_sync(0xffffffffu, rp_next, row - rp_base);
+                Acc xi[E];
+                if (t == 0 && chunk_ok) load_chunk<T, E>(Ain + (int64_t)row * K + q * E, xi);
+                Acc acc[E];
+#pragma unroll
+                for (int e = 0; e < E; ++e) acc[e] = Acc(0);
+                for (int32_t base = gb; base < e_end; base += 32) {
+                    const int32_t cnt = e_end - base < 32 ? e_end - base : 32;
+                    ensure((base + cnt - 1) >> 5);
+#pragma unroll
+                    for (int r = 0; r < GP; ++r) {
+                        const int sidx = r * TS + t;
+                        if (sidx < cnt && chunk_ok) {
+                            const Slot v = ring[(base + sidx) & (ST_RING - 1)];
+                            Acc x[E];
+                            load_chunk<T, E>(Ain + (int64_t)slot_col(v) * K + q * E, x);
+                            const Acc w = slot_w(v, Acc(0));
+#pragma unroll
+                            for (int e = 0; e < E; ++e) acc[e] = fma(w, x[e], acc[e]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int e = 0; e < E; ++e)
+#pragma unroll
+                    for (int o = GP; o < 32; o <<= 1) acc[e] += __shfl_xor_sync(0xffffffffu, acc[e], o);
+                if (t == 0 && chunk_ok) {
+                    const bool isolated = gb == e_end;
+                    Acc y[E];
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        const int k = q * E + e;
+                        Acc z = isolated ? xi[e] : one_m * xi[e] + omega * acc[e];
+                        y[e] = (z - st_sh[k]) * st_sh[K + k];
+                    }
+                    store_chunk<T, E>(Aout + (int64_t)row * K + q * E, y);
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        s1[e] += y[e];
+                        s2[e] += y[e] * y[e];
+                    }
+                }
+                gb = e_end;
+            }
+        }
+        cp_async_wait_all();
+    }
+    block_stats<Acc, K, E, G, LPR>(s1, s2, part, counter, n, stats_out);
+}
+
+// ---------------------------------------------------------------------------
+// Row-group sweep (the default sweep kernel).
+//
+// GP lanes serve one row (one 16-byte chunk of the K-wide vector row each),
+// so a warp runs 32 / GP consecutive rows at once; row groups go in
+// grid-stride order, so all warps work on one band of rows at a time and the
+// neighbour rows of banded graphs stay in L2.  Every lane reads the slot
+// entries of its row itself (the GP lanes of a row hit the same address, an
+// L1 broadcast), then gathers U neighbour chunks at once: no shuffles and no
+// predicated empty rounds.  The row pointers of the next two groups are loaded
+// ahead; keeping registers low (U = 2) buys more resident warps, which hides
+// the gather latency better than deeper per-warp prefetch did.
+// Slot indices are 32-bit (2m < 2^32) and rows 32-bit (n < 2^31).
+// ---------------------------------------------------------------------------
+template <typename T, int K, int U>
+__global__ void __launch_bounds__(SM_THREADS) k_sweep_row(
+    int64_t n64, const int64_t* __restrict__ rowptr, const typename SlotOf<T>::type* __restrict__ slots,
+    const T* __restrict__ Ain, T* __restrict__ Aout, double omega_d, const double* __restrict__ stats_in,
+    double* __restrict__ part, unsigned* __restrict__ counter, double* __restrict__ stats_out) {
+    using Slot = typename SlotOf<T>::type;
+    using L = RowLayout<T, K>;
+    using Acc = typename AccOf<T>::type;
+    constexpr int E = L::E, G = L::G, GP = L::GP;
+    constexpr int RPW = 32 / GP;
+    __shared__ Acc st_sh[2 * K];
+    const int n = (int)n64;
+    const int lane = threadIdx.x & 31;
+    const int seg = lane / GP, q = lane % GP;
+    const bool chunk_ok = q < G;
+    const Acc omega = (Acc)omega_d, one_m = (Acc)(1.0 - omega_d);
+    for (int i = threadIdx.x; i < 2 * K; i += blockDim.x) st_sh[i] = (Acc)stats_in[i];
+    __syncthreads();
+    Acc s1[E], s2[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) s1[e] = s2[e] = Acc(0);
+    const int stride = ((gridDim.x * blockDim.x) >> 5) * RPW;
+    int row = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * RPW + seg;
+    const T* Aq = Ain + q * E;
+    auto rp = [&](int r, unsigned& b, unsigned& e) {
+        if (r < n) {
+            b = (unsigned)__ldg(rowptr + r);
+            e = (unsigned)__ldg(rowptr + r + 1);
+        } else {
+            b = e = 0u;
+        }
+    };
+    unsigned b0, e0, b1, e1;
+    rp(row, b0, e0);
+    rp(row + stride, b1, e1);
+    const int gend = n + seg;  // the loop runs while this warp's group start is < n
+    for (; row < gend; row += stride) {
+        unsigned b2, e2;
+        rp(row + 2 * stride, b2, e2);
+        Slot v0[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (b0 + u < e0) v0[u] = __ldg(slots + b0 + u);
+        if (chunk_ok) {
+            Acc xi[E];
+            if (row < n) load_chunk<T, E>(Aq + (size_t)row * K, xi);
+            Acc acc[E];
+#pragma unroll
+            for (int e = 0; e < E; ++e) acc[e] = Acc(0);
+            {
+                Acc x[U][E];
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (b0 + u < e0) load_chunk<T, E>(Aq + (size_t)slot_col(v0[u]) * K, x[u]);
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (b0 + u < e0) {
+                        const Acc w = slot_w(v0[u], Acc(0));
+#pragma unroll
+                        for (int e = 0; e < E; ++e) acc[e] = fma(w, x[u][e], acc[e]);
+                    }
+            }
+            for (unsigned j = b0 + U; j < e0; j += U) {
+                Slot v[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (j + u < e0) v[u] = __ldg(slots + j + u);
+                Acc x[U][E];
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (j + u < e0) load_chunk<T, E>(Aq + (size_t)slot_col(v[u]) * K, x[u]);
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (j + u < e0) {
+                        const Acc w = slot_w(v[u], Acc(0));
+#pragma unroll
+                        for (int e = 0; e < E; ++e) acc[e] = fma(w, x[u][e], acc[e]);
+                    }
+            }
+            if (row < n) {
+                const bool isolated = b0 == e0;
+                Acc y[E];
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const int k = q * E + e;
+                    Acc z = isolated ? xi[e] : one_m * xi[e] + omega * acc[e];
+                    y[e] = (z - st_sh[k]) * st_sh[K + k];
+                }
+                store_chunk<T, E>(Aout + (size_t)row * K + q * E, y);
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    s1[e] += y[e];
+                    s2[e] += y[e] * y[e];
+                }
+            }
+        }
+        b0 = b1;
+        e0 = e1;
+        b1 = b2;
+        e1 = e2;
+    }
+    block_stats<Acc, K, E, G, GP>(s1, s2, part, counter, n64, stats_out);
+}
+
 // X = (A - mu) * inv_s, chunk-parallel
 template <typename T, int K>
 __global__ void k_apply(int64_t n, const T* __restrict__ A, T* __restrict__ X,
@@ -290,6 +587,107 @@ static cudaError_t launch_sweep(gr_ctx* c, int grid, const T* Ain, T* Aout, doub
     return cudaGetLastError();
 }
 
+// Streaming sweep when a group of 32 / GP rows would hold more slots than
+// four ring batches (long rows); the row-group kernel otherwise.
+template <typename T, int K>
+static bool stream_wide(const gr_ctx* c) {
+    constexpr int GP = RowLayout<T, K>::GP;
+    const double avg = c->n > 0 ? 2.0 * (double)c->m / (double)c->n : 0.0;
+    return GP < 32 && (32.0 / GP) * avg > 128.0;
+}
+
+template <typename T, int K, int LPR>
+static cudaError_t stream_occupancy(int* blocks_per_sm, size_t* dyn) {
+    using Slot = typename SlotOf<T>::type;
+    *dyn = sizeof(Slot) * (size_t)ST_RING * SM_WARPS;
+    static int cached = 0;
+    if (!cached) {
+        auto kern = k_sweep_stream<T, K, LPR>;
+        GR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*dyn));
+        GR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cached, kern, SM_THREADS, *dyn));
+        if (cached < 1) cached = 1;
+    }
+    *blocks_per_sm = cached;
+    return cudaSuccess;
+}
+
+template <typename T, int K, int LPR>
+static cudaError_t launch_sweep_stream_lpr(gr_ctx* c, const T* Ain, T* Aout, double omega, const double* st_in,
+                                           double* part, int part_cap, unsigned* counter, double* st_out) {
+    int bps = 1;
+    size_t dyn = 0;
+    GR_CUDA((stream_occupancy<T, K, LPR>(&bps, &dyn)));
+    int grid = c->num_sms * bps;
+    if (grid > part_cap) grid = part_cap;
+    const int64_t W = (int64_t)grid * SM_WARPS;
+    if (c->wpart_W != W) {
+        if (c->wpart) GR_CUDA(cudaFreeAsync(c->wpart, c->stream));
+        c->wpart = nullptr;
+        c->wpart_W = 0;
+        GR_CUDA(cudaMallocAsync(&c->wpart, sizeof(int32_t) * (size_t)(W + 1), c->stream));
+        k_warp_partition<<<(unsigned)ceil_div(W + 1, 256), 256, 0, c->stream>>>(c->n, c->rowptr, W, c->wpart);
+        count_launch();
+        c->wpart_W = W;
+    }
+    const typename SlotOf<T>::type* slots;
+    if constexpr (sizeof(T) == 8) {
+        if (!c->cw64) {
+            GR_CUDA(cudaMallocAsync(&c->cw64, sizeof(int4) * (size_t)(2 * c->m > 0 ? 2 * c->m : 1), c->stream));
+            if (c->m > 0) {
+                k_pack64<<<(unsigned)ceil_div(2 * c->m, 256), 256, 0, c->stream>>>(2 * c->m, c->col, c->wn64, c->cw64);
+                count_launch();
+            }
+        }
+        slots = c->cw64;
+    } else {
+        slots = c->cw32;
+    }
+    k_sweep_stream<T, K, LPR><<<grid, SM_THREADS, dyn, c->stream>>>(c->n, c->rowptr, slots, 2 * c->m, c->wpart,
+                                                                   Ain, Aout, omega, st_in, part, counter, st_out);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <typename T, int K>
+static cudaError_t launch_sweep_row(gr_ctx* c, const T* Ain, T* Aout, double omega, const double* st_in,
+                                    double* part, int part_cap, unsigned* counter, double* st_out) {
+    constexpr int U = 2;
+    static int bps = 0;
+    if (!bps) {
+        GR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_sweep_row<T, K, U>, SM_THREADS, 0));
+        if (bps < 1) bps = 1;
+    }
+    int grid = c->num_sms * bps;
+    if (grid > part_cap) grid = part_cap;
+    const typename SlotOf<T>::type* slots;
+    if constexpr (sizeof(T) == 8) {
+        if (!c->cw64) {
+            GR_CUDA(cudaMallocAsync(&c->cw64, sizeof(int4) * (size_t)(2 * c->m > 0 ? 2 * c->m : 1), c->stream));
+            if (c->m > 0) {
+                k_pack64<<<(unsigned)ceil_div(2 * c->m, 256), 256, 0, c->stream>>>(2 * c->m, c->col, c->wn64, c->cw64);
+                count_launch();
+            }
+        }
+        slots = c->cw64;
+    } else {
+        slots = c->cw32;
+    }
+    k_sweep_row<T, K, U><<<grid, SM_THREADS, 0, c->stream>>>(c->n, c->rowptr, slots, Ain, Aout, omega, st_in, part,
+                                                             counter, st_out);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// Sweep kernel choice: rows long enough to fill a warp -> streaming kernel;
+// short rows -> row-group kernel.
+template <typename T, int K>
+static cudaError_t launch_sweep_best(gr_ctx* c, const T* Ain, T* Aout, double omega, const double* st_in,
+                                     double* part, int part_cap, unsigned* counter, double* st_out) {
+    if (stream_wide<T, K>(c))
+        return launch_sweep_stream_lpr<T, K, 32>(c, Ain, Aout, omega, st_in, part, part_cap, counter, st_out);
+    return launch_sweep_row<T, K>(c, Ain, Aout, omega, st_in, part, part_cap, counter, st_out);
+}
+
 template <typename T, int K>
 static int pick_lpr(const gr_ctx* c) {
     constexpr int GP = RowLayout<T, K>::GP;
@@ -320,7 +718,9 @@ static cudaError_t run_smooth(gr_ctx* c, int sweeps, double omega, uint64_t seed
     const int init_rows = SM_WARPS * (32 / GP);
     const int64_t iwant = ceil_div(n, init_rows);
     const int igrid = (int)(iwant < cap ? (iwant > 0 ? iwant : 1) : cap);
-    const int maxgrid = grid > igrid ? grid : igrid;
+    // the streaming sweep runs a persistent grid of at most 8 blocks per SM
+    int maxgrid = grid > igrid ? grid : igrid;
+    if (c->num_sms * 8 > maxgrid) maxgrid = c->num_sms * 8;
     GR_CUDA(c->ws.get(WS_SMOOTH_PART, sizeof(double) * 2 * K * (size_t)maxgrid, &p_part));
     double* part = (double*)p_part;
     GR_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned), s));
@@ -333,16 +733,7 @@ static cudaError_t run_smooth(gr_ctx* c, int sweeps, double omega, uint64_t seed
     double* sin = st0;
     double* sout = st1;
     for (int it = 0; it < sweeps; ++it) {
-        cudaError_t e;
-        switch (lpr / GP) {
-            case 1: e = launch_sweep<T, K, GP>(c, grid, cur, nxt, omega, sin, part, counter, sout); break;
-            case 2: e = launch_sweep<T, K, (2 * GP <= 32 ? 2 * GP : 32)>(c, grid, cur, nxt, omega, sin, part, counter, sout); break;
-            case 4: e = launch_sweep<T, K, (4 * GP <= 32 ? 4 * GP : 32)>(c, grid, cur, nxt, omega, sin, part, counter, sout); break;
-            case 8: e = launch_sweep<T, K, (8 * GP <= 32 ? 8 * GP : 32)>(c, grid, cur, nxt, omega, sin, part, counter, sout); break;
-            case 16: e = launch_sweep<T, K, (16 * GP <= 32 ? 16 * GP : 32)>(c, grid, cur, nxt, omega, sin, part, counter, sout); break;
-            default: e = launch_sweep<T, K, 32>(c, grid, cur, nxt, omega, sin, part, counter, sout); break;
-        }
-        GR_CUDA(e);
+        GR_CUDA((launch_sweep_best<T, K>(c, cur, nxt, omega, sin, part, maxgrid, counter, sout)));
         const T* tmp = cur;
         cur = nxt;
         nxt = (T*)tmp;

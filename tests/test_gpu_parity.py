@@ -41,6 +41,9 @@ GRAPHS = {
     "path_iso": lambda: W.Graph(300, np.arange(0, 250, dtype=np.int32), np.arange(1, 251, dtype=np.int32),
                                 np.linspace(0.5, 2.0, 250)),  # nodes 251..299 isolated
     "mesh_ln": lambda: W.mesh3d(11, 7, 5, seed=4),
+    # long rows (mean degree >= 24): the streaming sweep kernel
+    "chunglu_s": lambda: W.chung_lu(3001, 60000, mean_deg=40.0, max_deg=600.0, seed=5),
+    "dense_rand": lambda: W.random_sparse(777, 15000, seed=6),
 }
 
 
