@@ -49,6 +49,22 @@ def parse_args():
     return ap.parse_args()
 
 
+def max_over_ranks(x, world, device=None):
+    """Max of a host float over all ranks (the slowest rank sets the time)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(edges_per_step, steps, world, t_max_ms):
+    """Input edges/s of the whole job: every rank reduces its own replica."""
+    return edges_per_step * steps * world / (t_max_ms / 1000.0)
+
+
 def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")), int(
         os.environ.get("WORLD_SIZE", "1"))
@@ -288,13 +304,9 @@ def main():
     launches = gr.graph_reduce_launch_count() - launches0
     clocks = sampler.stop()
     t_ms = ev0.elapsed_time(ev1)
-    t_max = t_ms
-    if world > 1:
-        tt = torch.tensor([t_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
+    t_max = max_over_ranks(t_ms, world, dev)
     edges_per_step = sum(s["m"] for s in all_stats[-1])
-    value = edges_per_step * args.steps * world / (t_max / 1000.0)
+    value = whole_job_value(edges_per_step, args.steps, world, t_max)
 
     # roofline of the dominant kernel: the Jacobi sweep (bytes / event time)
     sw_bytes = 0.0
@@ -345,11 +357,7 @@ def main():
             d2h = levels[-1].m * 16 + comp.numel() * 4
             del G, levels
         torch.cuda.synchronize()
-        te = time.perf_counter() - t0
-        if world > 1:
-            tt = torch.tensor([te], dtype=torch.float64, device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            te = float(tt.item())
+        te = max_over_ranks(time.perf_counter() - t0, world, dev)
         e2e = {"value": edges_per_step * k_e2e * world / te, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "steps": k_e2e}
 

@@ -252,14 +252,18 @@ def knn_indices(P: np.ndarray, k: int, device=None, chunk=4096):
         e = min(s + chunk, n)
         d2 = sq[s:e, None] - 2.0 * (Pt[s:e] @ Pt.T) + sq[None, :]
         cand[s:e] = torch.topk(d2, kk, dim=1, largest=False).indices.cpu().numpy()
-    # exact FP64 refinement over the candidates
-    diff = P[cand] - P[:, None, :]
-    dist2 = np.einsum("ijk,ijk->ij", diff, diff)
-    self_mask = cand == np.arange(n)[:, None]
-    dist2[self_mask] = np.inf
-    order = np.lexsort((cand, dist2), axis=1)[:, :k]
-    idx = np.take_along_axis(cand, order, 1)
-    dd = np.sqrt(np.take_along_axis(dist2, order, 1))
+    # exact FP64 refinement over the candidates (chunked)
+    idx = np.empty((n, k), np.int64)
+    dd = np.empty((n, k), np.float64)
+    for s in range(0, n, 65536):
+        e = min(s + 65536, n)
+        c = cand[s:e]
+        diff = P[c] - P[s:e, None, :]
+        dist2 = np.einsum("ijk,ijk->ij", diff, diff)
+        dist2[c == np.arange(s, e)[:, None]] = np.inf
+        order = np.lexsort((c, dist2), axis=1)[:, :k]
+        idx[s:e] = np.take_along_axis(c, order, 1)
+        dd[s:e] = np.sqrt(np.take_along_axis(dist2, order, 1))
     return idx, dd
 
 
