@@ -77,10 +77,6 @@ gr_status graph_reduce_create(gr_ctx** out, int64_t n, int64_t m, const int32_t*
     if (n < 1 || n >= (1ll << 31)) return set_error(nullptr, GR_EINVAL, "create: n must be in [1, 2^31)");
     if (m < 0 || m >= (1ll << 31)) return set_error(nullptr, GR_EINVAL, "create: m must be in [0, 2^31)");
     if (m > 0 && (!u || !v || !w)) return set_error(nullptr, GR_EINVAL, "create: edge arrays are NULL");
-    if (inputs_on_host && m > 0) {
-        std::string why;
-        if (!host_canonical(n, m, u, v, w, &why)) return set_error(nullptr, GR_EINVAL, "create: " + why);
-    }
     gr_ctx* c = new (std::nothrow) gr_ctx();
     if (!c) return set_error(nullptr, GR_ENOMEM, "create: host allocation failed");
     c->n = n;
@@ -105,7 +101,7 @@ gr_status graph_reduce_create(gr_ctx** out, int64_t n, int64_t m, const int32_t*
         graph_reduce_destroy(c);
         return e == cudaErrorMemoryAllocation ? GR_ENOMEM : GR_ECUDA;
     }
-    if (!inputs_on_host && m > 0) {
+    if (m > 0) {  // host or device inputs: checked on the device after the copy
         int32_t* bad = (int32_t*)(hs + 4);
         *bad = 0;
         void* dbad;
@@ -119,7 +115,11 @@ gr_status graph_reduce_create(gr_ctx** out, int64_t n, int64_t m, const int32_t*
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess || *bad) {
             if (e != cudaSuccess) cuda_error(nullptr, e, "create");
-            else set_error(nullptr, GR_EINVAL, "create: the edge list is not canonical (u < v < n, sorted, unique, w > 0 finite)");
+            else {
+                std::string why = "the edge list is not canonical (u < v < n, sorted, unique, w > 0 finite)";
+                if (inputs_on_host) host_canonical(n, m, u, v, w, &why);  // name the first bad edge
+                set_error(nullptr, GR_EINVAL, "create: " + why);
+            }
             graph_reduce_destroy(c);
             return e != cudaSuccess ? GR_ECUDA : GR_EINVAL;
         }

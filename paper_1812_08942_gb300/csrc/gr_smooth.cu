@@ -438,17 +438,61 @@ __global__ void __launch_bounds__(SM_THREADS) k_sweep_stream(
 // ---------------------------------------------------------------------------
 // Row-group sweep (the default sweep kernel).
 //
-// GP lanes serve one row (one 16-byte chunk of the K-wide vector row each),
-// so a warp runs 32 / GP consecutive rows at once; row groups go in
-// grid-stride order, so all warps work on one band of rows at a time and the
-// neighbour rows of banded graphs stay in L2.  Every lane reads the slot
-// entries of its row itself (the GP lanes of a row hit the same address, an
-// L1 broadcast), then gathers U neighbour chunks at once: no shuffles and no
-// predicated empty rounds.  The row pointers of the next two groups are loaded
-// ahead; keeping registers low (U = 2) buys more resident warps, which hides
-// the gather latency better than deeper per-warp prefetch did.
-// Slot indices are 32-bit (2m < 2^32) and rows 32-bit (n < 2^31).
+// G lanes serve one row (one 16-byte chunk of the K-wide vector row each), so
+// a warp runs RPW = floor(32 / G) consecutive rows at once (for K = 24 FP32:
+// 5 rows x 6 lanes, 30 of 32 lanes busy); row groups go in grid-stride order,
+// so all warps work on one band of rows at a time and the neighbour rows of
+// banded graphs stay in L2.  Every lane reads the slot entries of its row
+// itself (the G lanes of a row hit the same address, an L1 broadcast), then
+// gathers U neighbour chunks at once: no shuffles, no predicated empty
+// rounds.  The row pointers of the next two groups are loaded ahead; keeping
+// registers low buys resident warps, which hides the gather latency better
+// than deeper per-warp prefetch did.  Slot indices are 32-bit (2m < 2^32) and
+// rows 32-bit (n < 2^31).
 // ---------------------------------------------------------------------------
+template <typename Acc, int K, int E, int G>
+__device__ void block_stats_rows(Acc (&s1)[E], Acc (&s2)[E], double* __restrict__ part,
+                                 unsigned* __restrict__ counter, int64_t n, double* __restrict__ stats_out) {
+    __shared__ double wst[SM_WARPS][2 * K];
+    __shared__ bool last;
+    constexpr int RPW = 32 / G;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // lanes q < G collect the sums of lanes q + r G (same chunk, other rows)
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+#pragma unroll
+        for (int r = 1; r < RPW; ++r) {
+            const Acc a1 = __shfl_sync(0xffffffffu, s1[e], (lane + r * G) & 31);
+            const Acc a2 = __shfl_sync(0xffffffffu, s2[e], (lane + r * G) & 31);
+            if (lane < G) {
+                s1[e] += a1;
+                s2[e] += a2;
+            }
+        }
+    if (lane < G) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            wst[warp][lane * E + e] = (double)s1[e];
+            wst[warp][K + lane * E + e] = (double)s2[e];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 * K) {
+        double t = 0.0;
+        for (int w = 0; w < SM_WARPS; ++w) t += wst[w][threadIdx.x];
+        part[(int64_t)blockIdx.x * 2 * K + threadIdx.x] = t;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (last) {
+        __threadfence();
+        finish_stats<K>(part, gridDim.x, n, stats_out);
+        if (threadIdx.x == 0) *counter = 0u;
+    }
+}
+
 template <typename T, int K, int U>
 __global__ void __launch_bounds__(SM_THREADS) k_sweep_row(
     int64_t n64, const int64_t* __restrict__ rowptr, const typename SlotOf<T>::type* __restrict__ slots,
@@ -457,13 +501,13 @@ __global__ void __launch_bounds__(SM_THREADS) k_sweep_row(
     using Slot = typename SlotOf<T>::type;
     using L = RowLayout<T, K>;
     using Acc = typename AccOf<T>::type;
-    constexpr int E = L::E, G = L::G, GP = L::GP;
-    constexpr int RPW = 32 / GP;
+    constexpr int E = L::E, G = L::G;
+    constexpr int RPW = 32 / G;
     __shared__ Acc st_sh[2 * K];
     const int n = (int)n64;
     const int lane = threadIdx.x & 31;
-    const int seg = lane / GP, q = lane % GP;
-    const bool chunk_ok = q < G;
+    const int seg = lane / G, q = lane % G;
+    const bool lane_ok = seg < RPW;  // the last 32 mod G lanes idle
     const Acc omega = (Acc)omega_d, one_m = (Acc)(1.0 - omega_d);
     for (int i = threadIdx.x; i < 2 * K; i += blockDim.x) st_sh[i] = (Acc)stats_in[i];
     __syncthreads();
@@ -471,10 +515,10 @@ __global__ void __launch_bounds__(SM_THREADS) k_sweep_row(
 #pragma unroll
     for (int e = 0; e < E; ++e) s1[e] = s2[e] = Acc(0);
     const int stride = ((gridDim.x * blockDim.x) >> 5) * RPW;
-    int row = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * RPW + seg;
+    int row = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * RPW + (lane_ok ? seg : 0);
     const T* Aq = Ain + q * E;
     auto rp = [&](int r, unsigned& b, unsigned& e) {
-        if (r < n) {
+        if (r < n && lane_ok) {
             b = (unsigned)__ldg(rowptr + r);
             e = (unsigned)__ldg(rowptr + r + 1);
         } else {
@@ -484,34 +528,17 @@ __global__ void __launch_bounds__(SM_THREADS) k_sweep_row(
     unsigned b0, e0, b1, e1;
     rp(row, b0, e0);
     rp(row + stride, b1, e1);
-    const int gend = n + seg;  // the loop runs while this warp's group start is < n
+    const int gend = n + (lane_ok ? seg : 0);  // the loop runs while this warp's group start is < n
     for (; row < gend; row += stride) {
         unsigned b2, e2;
         rp(row + 2 * stride, b2, e2);
-        Slot v0[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-            if (b0 + u < e0) v0[u] = __ldg(slots + b0 + u);
-        if (chunk_ok) {
+        if (lane_ok) {
             Acc xi[E];
             if (row < n) load_chunk<T, E>(Aq + (size_t)row * K, xi);
             Acc acc[E];
 #pragma unroll
             for (int e = 0; e < E; ++e) acc[e] = Acc(0);
-            {
-                Acc x[U][E];
-#pragma unroll
-                for (int u = 0; u < U; ++u)
-                    if (b0 + u < e0) load_chunk<T, E>(Aq + (size_t)slot_col(v0[u]) * K, x[u]);
-#pragma unroll
-                for (int u = 0; u < U; ++u)
-                    if (b0 + u < e0) {
-                        const Acc w = slot_w(v0[u], Acc(0));
-#pragma unroll
-                        for (int e = 0; e < E; ++e) acc[e] = fma(w, x[u][e], acc[e]);
-                    }
-            }
-            for (unsigned j = b0 + U; j < e0; j += U) {
+            for (unsigned j = b0; j < e0; j += U) {
                 Slot v[U];
 #pragma unroll
                 for (int u = 0; u < U; ++u)
@@ -550,7 +577,7 @@ __global__ void __launch_bounds__(SM_THREADS) k_sweep_row(
         b1 = b2;
         e1 = e2;
     }
-    block_stats<Acc, K, E, G, GP>(s1, s2, part, counter, n64, stats_out);
+    block_stats_rows<Acc, K, E, G>(s1, s2, part, counter, n64, stats_out);
 }
 
 // X = (A - mu) * inv_s, chunk-parallel
