@@ -131,23 +131,13 @@ __device__ __forceinline__ Key key_inf() {
 // its own cluster, so the cluster-id gather is skipped; in the first round of
 // a pass every cluster is free, so the status gather is skipped too.
 template <bool D64, int LPC, bool FIRST_PASS>
-__global__ void k_propose(const int32_t* __restrict__ wl, const int32_t* __restrict__ wl_count,
-                          int32_t* __restrict__ next_count, const int64_t* __restrict__ rowptr,
-                          const int32_t* __restrict__ col, const int32_t* __restrict__ eid,
-                          const uint64_t* __restrict__ keys, const void* __restrict__ d,
-                          const int32_t* __restrict__ cl, const int32_t* __restrict__ nxt,
-                          uint8_t* __restrict__ status, int32_t* __restrict__ best, uint64_t* __restrict__ bhi,
-                          uint32_t* __restrict__ blo, uint64_t* __restrict__ tk_hi, uint32_t* __restrict__ tk_lo,
-                          int32_t* __restrict__ tk_nb, uint8_t* __restrict__ tk_cnt, int first_round,
-                          int32_t* __restrict__ err) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) *next_count = 0;
-    const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / LPC;
-    const int l = threadIdx.x % LPC;
-    const int count = *wl_count;
-    if (g >= count) return;
-    const unsigned gmask = LPC == 32 ? 0xffffffffu : (((1u << LPC) - 1u) << ((threadIdx.x & 31) / LPC * LPC));
-    const int gbase_lane = (threadIdx.x & 31) / LPC * LPC;
-    const int32_t c = wl[g];
+__device__ __forceinline__ void propose_one(
+    const int32_t c, const int l, const unsigned gmask, const int gbase_lane, const int64_t* __restrict__ rowptr,
+    const int32_t* __restrict__ col, const int32_t* __restrict__ eid, const uint64_t* __restrict__ keys,
+    const void* __restrict__ d, const int32_t* __restrict__ cl, const int32_t* __restrict__ nxt,
+    uint8_t* __restrict__ status, int32_t* __restrict__ best, uint64_t* __restrict__ bhi, uint32_t* __restrict__ blo,
+    uint64_t* __restrict__ tk_hi, uint32_t* __restrict__ tk_lo, int32_t* __restrict__ tk_nb,
+    uint8_t* __restrict__ tk_cnt, const int first_round, int32_t* __restrict__ err) {
     // 1) cached candidates
     const int cnt = first_round ? 0 : tk_cnt[c];
     if (cnt > 0) {
@@ -251,6 +241,28 @@ __global__ void k_propose(const int32_t* __restrict__ wl, const int32_t* __restr
     }
 }
 
+
+template <bool D64, int LPC, bool FIRST_PASS>
+__global__ void k_propose(const int32_t* __restrict__ wl, const int32_t* __restrict__ wl_count,
+                          int32_t* __restrict__ next_count, const int64_t* __restrict__ rowptr,
+                          const int32_t* __restrict__ col, const int32_t* __restrict__ eid,
+                          const uint64_t* __restrict__ keys, const void* __restrict__ d,
+                          const int32_t* __restrict__ cl, const int32_t* __restrict__ nxt,
+                          uint8_t* __restrict__ status, int32_t* __restrict__ best, uint64_t* __restrict__ bhi,
+                          uint32_t* __restrict__ blo, uint64_t* __restrict__ tk_hi, uint32_t* __restrict__ tk_lo,
+                          int32_t* __restrict__ tk_nb, uint8_t* __restrict__ tk_cnt, int first_round,
+                          int32_t* __restrict__ err) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *next_count = 0;
+    const int l = threadIdx.x % LPC;
+    const unsigned gmask = LPC == 32 ? 0xffffffffu : (((1u << LPC) - 1u) << ((threadIdx.x & 31) / LPC * LPC));
+    const int gbase_lane = (threadIdx.x & 31) / LPC * LPC;
+    const int count = *wl_count;
+    const int64_t groups = ((int64_t)gridDim.x * blockDim.x) / LPC;
+    for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / LPC; g < count; g += groups)
+        propose_one<D64, LPC, FIRST_PASS>(wl[g], l, gmask, gbase_lane, rowptr, col, eid, keys, d, cl, nxt, status,
+                                          best, bhi, blo, tk_hi, tk_lo, tk_nb, tk_cnt, first_round, err);
+}
+
 // Mutual best pointers merge; the rest stays on the worklist.
 __global__ void k_accept(const int32_t* __restrict__ wl, const int32_t* __restrict__ wl_count,
                          int32_t* __restrict__ wl_next, int32_t* __restrict__ next_count,
@@ -259,23 +271,25 @@ __global__ void k_accept(const int32_t* __restrict__ wl, const int32_t* __restri
                          int32_t* __restrict__ pc, int32_t* __restrict__ pb,
                          uint64_t* __restrict__ phi, uint32_t* __restrict__ plo,
                          int32_t* __restrict__ npairs) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= *wl_count) return;
-    const int32_t c = wl[i];
-    if (status[c] != ST_FREE) return;  // dead this round
-    const int32_t b = best[c];
-    const bool matched = best[b] == c;
-    if (matched) {
-        status[c] = ST_MATCHED;
-        if (c < b) {
-            int32_t k = atomicAdd(npairs, 1);
-            pc[k] = c;
-            pb[k] = b;
-            phi[k] = bhi[c];
-            plo[k] = blo[c];
+    const int count = *wl_count;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
+        const int32_t c = wl[i];
+        if (status[c] != ST_FREE) continue;  // dead this round
+        const int32_t b = best[c];
+        const bool matched = best[b] == c;
+        if (matched) {
+            status[c] = ST_MATCHED;
+            if (c < b) {
+                int32_t k = atomicAdd(npairs, 1);
+                pc[k] = c;
+                pb[k] = b;
+                phi[k] = bhi[c];
+                plo[k] = blo[c];
+            }
         }
+        warp_append(!matched, c, wl_next, next_count);
     }
-    warp_append(!matched, c, wl_next, next_count);
 }
 
 __global__ void k_pairs_keys(int32_t npairs, const uint64_t* __restrict__ phi,
@@ -334,7 +348,9 @@ __global__ void k_gather_u64(const uint64_t* __restrict__ src, const uint32_t* _
 template <bool D64, int LPC, bool FIRST_PASS>
 static void launch_propose(gr_ctx* c, AggState& S, int r, int64_t bound, const void* d) {
     const int64_t threads = bound * LPC;
-    const unsigned grid = (unsigned)(threads > 0 ? ceil_div(threads, 256) : 1);
+    int64_t want = threads > 0 ? ceil_div(threads, 256) : 1;
+    const int64_t cap = (int64_t)c->num_sms * 8;
+    const unsigned grid = (unsigned)(want < cap ? want : cap);
     k_propose<D64, LPC, FIRST_PASS><<<grid, 256, 0, c->stream>>>(
         S.wl[r & 1], S.ctr + (r & 1), S.ctr + ((r + 1) & 1), c->rowptr, c->col, c->eid, S.keys, d, S.cl, S.nxt,
         S.status, S.best, S.bhi, S.blo, S.tk_hi, S.tk_lo, S.tk_nb, S.tk_cnt, r == 0 ? 1 : 0, S.ctr + 3);
@@ -416,7 +432,7 @@ gr_status aggregate_impl(gr_ctx* c, const void* d, int d_is_f64, int64_t target_
         int64_t nlive = n_cur;
         int r = 0;
         while (nlive > 0) {
-            const int batch = r < 2 ? 1 : 4;
+            const int batch = 6;  // rounds between readbacks; a round on an empty list is two tiny launches
             for (int bi = 0; bi < batch; ++bi, ++r) {
                 const bool fp = pass == 0;
                 if (d_is_f64) {
@@ -428,7 +444,8 @@ gr_status aggregate_impl(gr_ctx* c, const void* d, int d_is_f64, int64_t target_
                     else if (lpc == 8) launch_propose_pass<false, 8>(c, S, r, nlive, d, fp);
                     else launch_propose_pass<false, 4>(c, S, r, nlive, d, fp);
                 }
-                k_accept<<<(unsigned)ceil_div(nlive, 256), 256, 0, s>>>(
+                const int64_t acap = (int64_t)c->num_sms * 8, awant = ceil_div(nlive, 256);
+                k_accept<<<(unsigned)(awant < acap ? awant : acap), 256, 0, s>>>(
                     S.wl[r & 1], S.ctr + (r & 1), S.wl[(r + 1) & 1], S.ctr + ((r + 1) & 1), S.status,
                     S.best, S.bhi, S.blo, S.pc, S.pb, S.phi, S.plo, S.ctr + 2); count_launch();
             }
