@@ -331,7 +331,7 @@ def main():
     per_level = []
     for s in all_stats[-1]:
         t = s["t_smooth"] + s["t_affinity"] + s["t_aggregate"] + s["t_coarsen"]
-        per_level.append({"n": s["n"], "m": s["m"], "nc": s["nc"], "mc": s["mc"], "rounds": s["rounds"],
+        per_level.append({"n": s["n"], "m": s["m"], "nc": s["nc"], "mc": s["mc"], "proposals": s["proposals"],
                           "t_smooth_ms": round(s["t_smooth"], 4), "t_affinity_ms": round(s["t_affinity"], 4),
                           "t_aggregate_ms": round(s["t_aggregate"], 4), "t_coarsen_ms": round(s["t_coarsen"], 4),
                           "edges_per_s": s["m"] / (t / 1000.0) if t > 0 else None})

@@ -50,7 +50,7 @@ typedef enum {
     GR_EINVAL = 1,    /* invalid argument or non-canonical graph            */
     GR_ENOMEM = 2,    /* device allocation failed                           */
     GR_ECUDA = 3,     /* CUDA runtime error                                 */
-    GR_ETIMEOUT = 4,  /* aggregation exceeded its handshake round limit     */
+    GR_ETIMEOUT = 4,  /* aggregation exceeded its proposal budget           */
     GR_ESTATE = 5     /* call not valid for this context                    */
 } gr_status;
 
@@ -123,19 +123,22 @@ gr_status graph_reduce_affinity(gr_ctx* ctx, const void* X, int K, gr_prec prec,
  * scheme; this one is greedy matching in ascending (d, edge id) order, run in
  * `passes` passes on the cluster graph (the key of a cluster pair is its
  * smallest fine (d, id)), each pass making at most n_cur - target_nc merges and
- * passes stopping once n_cur <= target_nc.  Computed by rounds of a lock-free
- * handshake (mutual best neighbours merge), which yields exactly the greedy
+ * passes stopping once n_cur <= target_nc.  Computed per pass by the suitor
+ * algorithm (Manne & Halappanavar 2014: lock-free proposals, each cluster
+ * keeping the best key proposed to it), which yields exactly the greedy
  * matching.  Coarse label = rank of the aggregate's smallest fine node.
- *   d            device, m distances (double if d_is_f64 else float), >= 0
- *   target_nc    >= 1
- *   max_rounds   handshake rounds allowed per pass (<= 0: n + 64)
- *   agg_out      device, n labels in [0, nc)
- *   nc_out       host, number of aggregates
- *   rounds_out   host, total handshake rounds, or NULL
- * GR_ETIMEOUT if a pass needs more than max_rounds rounds. */
+ *   d              device, m distances (double if d_is_f64 else float), >= 0
+ *   target_nc      >= 1
+ *   max_proposals  budget of proposals (successful or not) per pass; <= 0:
+ *                  no budget.  A pass makes at least one per matched cluster.
+ *   agg_out        device, n labels in [0, nc)
+ *   nc_out         host, number of aggregates
+ *   proposals_out  host, total proposals over all passes, or NULL
+ * GR_ETIMEOUT if a pass made more than max_proposals proposals (its work is
+ * done; the outputs are unspecified). */
 gr_status graph_reduce_aggregate(gr_ctx* ctx, const void* d, int d_is_f64, int64_t target_nc,
-                                 int passes, int max_rounds, int32_t* agg_out, int64_t* nc_out,
-                                 int32_t* rounds_out);
+                                 int passes, int64_t max_proposals, int32_t* agg_out, int64_t* nc_out,
+                                 int64_t* proposals_out);
 
 /* Galerkin reduced graph L_R = H_G^R L_G H_R^G (Sec. 3.2.2) with H_R^G = P,
  * P[i, agg[i]] = 1, H_G^R = P^T: one reduced edge (A < B) per pair of
@@ -167,7 +170,7 @@ typedef struct gr_params {
     int level_ratio;       /* level target = max(ceil(n/level_ratio), final)  */
     int64_t final_target;  /* stop once n <= final_target                     */
     int max_levels;        /* capacity of levels_out                          */
-    int max_rounds;        /* handshake round limit per pass (<= 0: default)  */
+    int64_t max_proposals; /* aggregation proposal budget per pass (<= 0: none) */
 } gr_params;
 
 /* Per-level record filled by graph_reduce_multilevel (host).  Times are CUDA
@@ -175,7 +178,7 @@ typedef struct gr_params {
  * only the `sweeps` Jacobi sweep kernels inside t_smooth. */
 typedef struct gr_level_stats {
     int64_t n, m, nc, mc;
-    int32_t rounds;
+    int64_t proposals;     /* aggregation proposals over all passes */
     int32_t sweeps;
     float t_smooth, t_affinity, t_aggregate, t_coarsen;
     float t_sweeps;

@@ -38,12 +38,12 @@ class gr_params(ctypes.Structure):
     _fields_ = [("K", ctypes.c_int), ("sweeps", ctypes.c_int), ("omega", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("prec", ctypes.c_int), ("passes", ctypes.c_int),
                 ("level_ratio", ctypes.c_int), ("final_target", ctypes.c_int64),
-                ("max_levels", ctypes.c_int), ("max_rounds", ctypes.c_int)]
+                ("max_levels", ctypes.c_int), ("max_proposals", ctypes.c_int64)]
 
 
 class gr_level_stats(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("m", ctypes.c_int64), ("nc", ctypes.c_int64), ("mc", ctypes.c_int64),
-                ("rounds", ctypes.c_int32), ("sweeps", ctypes.c_int32), ("t_smooth", ctypes.c_float),
+                ("proposals", ctypes.c_int64), ("sweeps", ctypes.c_int32), ("t_smooth", ctypes.c_float),
                 ("t_affinity", ctypes.c_float), ("t_aggregate", ctypes.c_float), ("t_coarsen", ctypes.c_float),
                 ("t_sweeps", ctypes.c_float)]
 
@@ -69,7 +69,7 @@ def load():
         "graph_reduce_smooth": (I, [P, I, I, D, U64, I, I, P]),
         "graph_reduce_smooth_noalloc": (I, [P, I, I, D, U64, I, I, P]),
         "graph_reduce_affinity": (I, [P, P, I, I, P, P]),
-        "graph_reduce_aggregate": (I, [P, P, I, I64, I, I, P, ctypes.POINTER(I64), ctypes.POINTER(I32)]),
+        "graph_reduce_aggregate": (I, [P, P, I, I64, I, I64, P, ctypes.POINTER(I64), ctypes.POINTER(I64)]),
         "graph_reduce_coarsen": (I, [P, P, I64, PP]),
         "graph_reduce_get_edges": (I, [P, ctypes.POINTER(I64), P, P, P, I]),
         "graph_reduce_get_map": (I, [P, P, ctypes.POINTER(I64)]),
@@ -186,18 +186,18 @@ def graph_reduce_affinity(g: Graph, X, d_out, a_out=None):
     return d_out
 
 
-def graph_reduce_aggregate(g: Graph, d, target_nc, passes=2, max_rounds=0, agg_out=None):
-    """Returns (agg, nc, rounds)."""
+def graph_reduce_aggregate(g: Graph, d, target_nc, passes=2, max_proposals=0, agg_out=None):
+    """Returns (agg, nc, proposals)."""
     assert d.is_cuda and d.numel() == g.m and d.dtype in (torch.float32, torch.float64)
     if agg_out is None:
         agg_out = torch.empty(g.n, dtype=torch.int32, device=d.device)
     nc = ctypes.c_int64(0)
-    rounds = ctypes.c_int32(0)
+    proposals = ctypes.c_int64(0)
     st = load().graph_reduce_aggregate(g.handle, _ptr(d), 1 if d.dtype == torch.float64 else 0, int(target_nc),
-                                       int(passes), int(max_rounds), _ptr(agg_out), ctypes.byref(nc),
-                                       ctypes.byref(rounds))
+                                       int(passes), int(max_proposals), _ptr(agg_out), ctypes.byref(nc),
+                                       ctypes.byref(proposals))
     _check(st, g.handle)
-    return agg_out, int(nc.value), int(rounds.value)
+    return agg_out, int(nc.value), int(proposals.value)
 
 
 def graph_reduce_coarsen(g: Graph, agg, nc) -> Graph:
@@ -245,11 +245,11 @@ class ReduceParams:
     level_ratio: int = 4
     final_target: int = 1
     max_levels: int = 32
-    max_rounds: int = 0
+    max_proposals: int = 0
 
     def to_c(self):
         return gr_params(self.K, self.sweeps, self.omega, self.seed, self.prec, self.passes, self.level_ratio,
-                         self.final_target, self.max_levels, self.max_rounds)
+                         self.final_target, self.max_levels, self.max_proposals)
 
 
 def graph_reduce_multilevel(g: Graph, params: ReduceParams, want_stats=True):
@@ -270,7 +270,7 @@ def graph_reduce_multilevel(g: Graph, params: ReduceParams, want_stats=True):
     if want_stats:
         for i in range(nl.value):
             s = stats[i]
-            out.append(dict(n=s.n, m=s.m, nc=s.nc, mc=s.mc, rounds=s.rounds, sweeps=s.sweeps, t_smooth=s.t_smooth,
+            out.append(dict(n=s.n, m=s.m, nc=s.nc, mc=s.mc, proposals=s.proposals, sweeps=s.sweeps, t_smooth=s.t_smooth,
                             t_affinity=s.t_affinity, t_aggregate=s.t_aggregate, t_coarsen=s.t_coarsen,
                             t_sweeps=s.t_sweeps))
     return levels, out

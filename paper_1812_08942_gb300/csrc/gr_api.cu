@@ -162,13 +162,14 @@ gr_status graph_reduce_affinity(gr_ctx* ctx, const void* X, int K, gr_prec prec,
 }
 
 gr_status graph_reduce_aggregate(gr_ctx* ctx, const void* d, int d_is_f64, int64_t target_nc, int passes,
-                                 int max_rounds, int32_t* agg_out, int64_t* nc_out, int32_t* rounds_out) {
+                                 int64_t max_proposals, int32_t* agg_out, int64_t* nc_out,
+                                 int64_t* proposals_out) {
     if (!ctx) return set_error(nullptr, GR_EINVAL, "aggregate: ctx is NULL");
     if (!agg_out || !nc_out || (ctx->m > 0 && !d)) return set_error(ctx, GR_EINVAL, "aggregate: NULL argument");
     if (target_nc < 1 || passes < 0 || passes > 30)
         return set_error(ctx, GR_EINVAL, "aggregate: need target_nc >= 1 and 0 <= passes <= 30");
-    if (rounds_out) *rounds_out = 0;
-    return aggregate_impl(ctx, d, d_is_f64, target_nc, passes, max_rounds, agg_out, nc_out, rounds_out);
+    if (proposals_out) *proposals_out = 0;
+    return aggregate_impl(ctx, d, d_is_f64, target_nc, passes, max_proposals, agg_out, nc_out, proposals_out);
 }
 
 gr_status graph_reduce_coarsen(gr_ctx* ctx, const int32_t* agg, int64_t nc, gr_ctx** coarse_out) {
@@ -248,10 +249,10 @@ gr_status graph_reduce_multilevel(gr_ctx* fine, const gr_params* p, gr_ctx** lev
         int64_t target = (cur->n + p->level_ratio - 1) / p->level_ratio;
         if (target < p->final_target) target = p->final_target;
         int64_t nc = 0;
-        int32_t rounds = 0;
+        int64_t proposals = 0;
         if (st == GR_OK)
-            st = aggregate_impl(cur, pd, prec == GR_F64, target, p->passes, p->max_rounds, (int32_t*)pa, &nc,
-                                &rounds);
+            st = aggregate_impl(cur, pd, prec == GR_F64, target, p->passes, p->max_proposals, (int32_t*)pa, &nc,
+                                &proposals);
         if (timed) cudaEventRecord(ev[3], s);
         if (st != GR_OK) {
             if (cur != fine) fine->last_error = cur->last_error;
@@ -272,7 +273,7 @@ gr_status graph_reduce_multilevel(gr_ctx* fine, const gr_params* p, gr_ctx** lev
             L.m = cur->m;
             L.nc = next->n;
             L.mc = next->m;
-            L.rounds = rounds;
+            L.proposals = proposals;
             cudaEventElapsedTime(&L.t_smooth, ev[0], ev[1]);
             cudaEventElapsedTime(&L.t_affinity, ev[1], ev[2]);
             cudaEventElapsedTime(&L.t_aggregate, ev[2], ev[3]);

@@ -114,7 +114,7 @@ gr_status smooth_impl(gr_ctx* c, int K, int sweeps, double omega, uint64_t seed,
                       cudaEvent_t ev_end = nullptr);
 gr_status affinity_impl(gr_ctx* c, const void* X, int K, gr_prec prec, void* d, void* a);
 gr_status aggregate_impl(gr_ctx* c, const void* d, int d_is_f64, int64_t target_nc, int passes,
-                         int max_rounds, int32_t* agg, int64_t* nc_out, int32_t* rounds_out);
+                         int64_t max_proposals, int32_t* agg, int64_t* nc_out, int64_t* proposals_out);
 gr_status coarsen_impl(gr_ctx* c, const int32_t* agg, int64_t nc, gr_ctx** out);
 gr_status loss_fwd_impl(gr_ctx* fine, gr_ctx* coarse, const int32_t* agg, const float* X, int K,
                         const float* w_c, int sweeps, double omega, float* loss, float* saved);

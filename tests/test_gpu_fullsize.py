@@ -56,7 +56,7 @@ def _level_checks(gr, oracle_mod, g, K, S, omega=0.7, target_div=4, sample=200_0
     assert np.max(np.abs(dh[idx].astype(np.float64) - dref)) <= 1e-5
     # aggregation: the complete map from the GPU's own distances
     target = -(-g.n // target_div)
-    agg, nc, rounds = gr.graph_reduce_aggregate(G, d, target, 2)
+    agg, nc, proposals = gr.graph_reduce_aggregate(G, d, target, 2)
     ragg, rnc = oracle_mod.aggregate(g.n, g.u, g.v, dh.astype(np.float64), target, 2)
     assert nc == rnc and np.array_equal(agg.cpu().numpy(), ragg)
     # Galerkin: the complete reduced graph
@@ -65,18 +65,18 @@ def _level_checks(gr, oracle_mod, g, K, S, omega=0.7, target_div=4, sample=200_0
     cu, cv, cw = (t.numpy() for t in gr.graph_reduce_get_edges(C, on_host=True))
     assert np.array_equal(cu, uc) and np.array_equal(cv, vc)
     assert np.max(np.abs(cw - wc) / wc) <= 1e-6
-    return nc, rounds
+    return nc, proposals
 
 
 def test_mesh128_fullsize_level(gr, oracle_mod):
     g = W.mesh3d(128, 128, 128)
-    nc, rounds = _level_checks(gr, oracle_mod, g, K=24, S=8)
+    nc, proposals = _level_checks(gr, oracle_mod, g, K=24, S=8)
     assert 0.25 * g.n <= nc < 0.5 * g.n
 
 
 def test_chunglu434k_fullsize_level(gr, oracle_mod):
     g = W.chung_lu()
-    nc, rounds = _level_checks(gr, oracle_mod, g, K=16, S=5)
+    nc, proposals = _level_checks(gr, oracle_mod, g, K=16, S=5)
     assert nc < 0.5 * g.n
 
 

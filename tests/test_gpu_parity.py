@@ -173,7 +173,7 @@ def test_aggregate_bitexact_oracle_d(gr, oracle_mod, case):
     d = oracle_mod.affinity(g.n, g.u, g.v, X)
     ref, rnc = oracle_mod.aggregate(g.n, g.u, g.v, d, target, passes)
     G = gr.graph_reduce_create(g.n, g.u, g.v, g.w)
-    agg, nc, rounds = gr.graph_reduce_aggregate(G, torch.from_numpy(d).to(DEV), target, passes)
+    agg, nc, _ = gr.graph_reduce_aggregate(G, torch.from_numpy(d).to(DEV), target, passes)
     assert nc == rnc
     assert np.array_equal(agg.cpu().numpy(), ref)
     # FP32 keys: the same order as the oracle run on the FP32-rounded distances
@@ -191,17 +191,17 @@ def test_aggregate_ties_and_errors(gr, oracle_mod):
         ref, rnc = oracle_mod.aggregate(g.n, g.u, g.v, d, target, passes)
         agg, nc, _ = gr.graph_reduce_aggregate(G, torch.from_numpy(d).to(DEV), target, passes)
         assert nc == rnc and np.array_equal(agg.cpu().numpy(), ref)
-    # a path with increasing distances needs one round per merge: the round
-    # limit turns that into GR_ETIMEOUT instead of running on
+    # a pass makes at least one proposal per matched node (64 on this path):
+    # a budget of 3 turns that into GR_ETIMEOUT
     p = W.path(64)
     P = gr.graph_reduce_create(p.n, p.u, p.v, p.w)
     dp = torch.linspace(0.01, 0.9, p.m, dtype=torch.float64, device=DEV)
     with pytest.raises(gr.GraphReduceError) as ei:
-        gr.graph_reduce_aggregate(P, dp, 1, 1, max_rounds=3)
+        gr.graph_reduce_aggregate(P, dp, 1, 1, max_proposals=3)
     assert ei.value.status == 4
-    agg, nc, rounds = gr.graph_reduce_aggregate(P, dp, 1, 1)
+    agg, nc, proposals = gr.graph_reduce_aggregate(P, dp, 1, 1)
     ref, rnc = oracle_mod.aggregate(p.n, p.u, p.v, dp.cpu().numpy(), 1, 1)
-    assert nc == rnc and np.array_equal(agg.cpu().numpy(), ref) and rounds >= 32
+    assert nc == rnc and np.array_equal(agg.cpu().numpy(), ref) and proposals >= 64
     with pytest.raises(gr.GraphReduceError) as ei:
         gr.graph_reduce_aggregate(P, -dp, 1, 1)
     assert ei.value.status == 1
@@ -262,7 +262,7 @@ def test_multilevel_f64_eigs(gr, oracle_mod, shape, final):
     assert np.max(np.abs(ev_gpu - ev_ref) / ev_ref) <= 1e-3
     comp = gr.graph_reduce_compose_maps(glev).cpu().numpy()
     assert np.array_equal(comp, oracle_mod.compose_maps(levels))
-    assert all(s["rounds"] > 0 for s in stats)
+    assert all(s["proposals"] > 0 for s in stats)
 
 
 # ---------------------------------------------------------------------------
