@@ -60,20 +60,6 @@ __global__ void k_agg_init(int64_t n, int32_t* __restrict__ cl, int32_t* __restr
     tail[i] = (int32_t)i;
 }
 
-// Append `item` to a worklist when `keep`: one atomic per warp, entries of a
-// warp stay contiguous and in lane order (keeps neighbouring rows together).
-__device__ __forceinline__ int32_t warp_slot(bool keep, int32_t* __restrict__ count) {
-    const unsigned active = __activemask();
-    const unsigned ball = __ballot_sync(active, keep);
-    if (!ball) return -1;
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(ball) - 1;
-    int32_t base = 0;
-    if (lane == leader) base = atomicAdd(count, __popc(ball));
-    base = __shfl_sync(active, base, leader);
-    return keep ? base + __popc(ball & ((1u << lane) - 1u)) : -1;
-}
-
 // Per-slot keys for FP32 distances: (float bits << 32 | edge id) of the slot's
 // edge, so the scans read one coalesced 8-byte key per slot.
 __global__ void k_slot_keys(int64_t slots, const int32_t* __restrict__ eid, const float* __restrict__ d,
@@ -111,77 +97,86 @@ __device__ __forceinline__ bool key_is_inf(const Key& k) { return k.hi == ~0ull;
 // (atomicMin is the proposal); FP64 distances -> the edge id (-1 none) of the
 // key, replaced by compare-and-swap after comparing (d, id).
 // ---------------------------------------------------------------------------
-template <bool D64>
-__device__ __forceinline__ Key key_of_edge(const void* __restrict__ d, int32_t e) {
+__device__ __forceinline__ Key key_of_edge64(const double* __restrict__ d, int32_t e) {
     Key k;
-    if constexpr (D64) {
-        const double x = __ldg((const double*)d + e);
-        k.hi = x == 0.0 ? 0ull : (uint64_t)__double_as_longlong(x);
-        k.lo = (uint32_t)e;
-    } else {
-        const float x = __ldg((const float*)d + e);
-        const uint64_t b = x == 0.f ? 0ull : (uint64_t)(uint32_t)__float_as_int(x);
-        k.hi = (b << 32) | (uint64_t)(uint32_t)e;
-        k.lo = 0u;
-    }
+    const double x = __ldg(d + e);
+    k.hi = x == 0.0 ? 0ull : (uint64_t)__double_as_longlong(x);
+    k.lo = (uint32_t)e;
     return k;
 }
 
+// Key handling per distance precision.  FP32: the packed 64-bit key itself,
+// compared as an integer, and ws holds it (the proposal is an atomicMin).
+// FP64: (double bits, edge id), and ws holds the edge id (compare-and-swap
+// after comparing keys).
 template <bool D64>
-__device__ __forceinline__ int32_t key_edge(const Key& k) {
-    return D64 ? (int32_t)k.lo : (int32_t)(uint32_t)k.hi;
-}
+struct SK;
 
-template <bool D64>
-__device__ __forceinline__ Key slot_key(int64_t j, const int32_t* __restrict__ eid, const uint64_t* __restrict__ keys,
-                                        const void* __restrict__ d, int32_t* __restrict__ err) {
-    if constexpr (D64) {
+template <>
+struct SK<false> {
+    using K = unsigned long long;
+    static __device__ __forceinline__ K inf() { return ~0ull; }
+    static __device__ __forceinline__ bool less(K a, K b) { return a < b; }
+    static __device__ __forceinline__ bool is_inf(K a) { return a == ~0ull; }
+    static __device__ __forceinline__ int32_t edge(K a) { return (int32_t)(uint32_t)a; }
+    static __device__ __forceinline__ uint64_t hi(K a) { return a; }
+    static __device__ __forceinline__ uint32_t lo(K) { return 0u; }
+    static __device__ __forceinline__ K slot(int64_t j, const int32_t* __restrict__, const uint64_t* __restrict__ keys,
+                                             const void* __restrict__, int32_t*) {
+        return keys[j];
+    }
+    // current suitor key of cluster b, read from L2 (other blocks update it)
+    static __device__ __forceinline__ K load(const void* ws, const void* __restrict__, int32_t b) {
+        return __ldcg((const unsigned long long*)ws + b);
+    }
+    // true if k is now b's key; old = the key it displaced (inf if none) or,
+    // on failure, the smaller key that holds b
+    static __device__ __forceinline__ bool propose(void* ws, const void* __restrict__, int32_t b, K k, K& old) {
+        old = atomicMin((unsigned long long*)ws + b, k);
+        return old > k;
+    }
+    static __device__ __forceinline__ K shfl_xor(unsigned mask, K a, int o, int w) {
+        return __shfl_xor_sync(mask, a, o, w);
+    }
+};
+
+template <>
+struct SK<true> {
+    using K = Key;
+    static __device__ __forceinline__ K inf() { return key_inf(); }
+    static __device__ __forceinline__ bool less(const K& a, const K& b) { return key_less(a, b); }
+    static __device__ __forceinline__ bool is_inf(const K& a) { return key_is_inf(a); }
+    static __device__ __forceinline__ int32_t edge(const K& a) { return (int32_t)a.lo; }
+    static __device__ __forceinline__ uint64_t hi(const K& a) { return a.hi; }
+    static __device__ __forceinline__ uint32_t lo(const K& a) { return a.lo; }
+    static __device__ __forceinline__ K slot(int64_t j, const int32_t* __restrict__ eid, const uint64_t* __restrict__,
+                                             const void* __restrict__ d, int32_t* err) {
         return make_key<true>(d, eid[j], err);
-    } else {
-        Key k;
-        k.hi = keys[j];
-        k.lo = 0u;
-        return k;
     }
-}
-
-// current suitor key of cluster b, read from L2 (other blocks update it)
-template <bool D64>
-__device__ __forceinline__ Key ws_load(const void* ws, const void* __restrict__ d, int32_t b) {
-    if constexpr (D64) {
+    static __device__ __forceinline__ K load(const void* ws, const void* __restrict__ d, int32_t b) {
         const int32_t e = __ldcg((const int32_t*)ws + b);
-        return e < 0 ? key_inf() : key_of_edge<true>(d, e);
-    } else {
-        Key k;
-        k.hi = __ldcg((const unsigned long long*)ws + b);
-        k.lo = k.hi == ~0ull ? ~0u : 0u;
-        return k;
+        return e < 0 ? key_inf() : key_of_edge64((const double*)d, e);
     }
-}
-
-// Propose key k to cluster b.  True if k is now b's key; `old` is the key it
-// displaced (inf if none), or on failure the smaller key that holds b.
-template <bool D64>
-__device__ __forceinline__ bool ws_propose(void* ws, const void* __restrict__ d, int32_t b, const Key& k,
-                                           Key& old) {
-    if constexpr (D64) {
+    static __device__ __forceinline__ bool propose(void* ws, const void* __restrict__ d, int32_t b, const K& k,
+                                                   K& old) {
         int32_t* w = (int32_t*)ws + b;
         int32_t cur = __ldcg(w);
         // every failed swap sees a strictly smaller key, so this ends within deg(b) + 1 tries
         while (true) {
-            old = cur < 0 ? key_inf() : key_of_edge<true>(d, cur);
+            old = cur < 0 ? key_inf() : key_of_edge64((const double*)d, cur);
             if (!key_less(k, old)) return false;
             const int32_t prev = atomicCAS(w, cur, (int32_t)k.lo);
             if (prev == cur) return true;
             cur = prev;
         }
-    } else {
-        const unsigned long long o = atomicMin((unsigned long long*)ws + b, (unsigned long long)k.hi);
-        old.hi = o;
-        old.lo = o == ~0ull ? ~0u : 0u;
-        return o > k.hi;
     }
-}
+    static __device__ __forceinline__ K shfl_xor(unsigned mask, const K& a, int o, int w) {
+        K r;
+        r.hi = __shfl_xor_sync(mask, a.hi, o, w);
+        r.lo = __shfl_xor_sync(mask, a.lo, o, w);
+        return r;
+    }
+};
 
 // the cluster at the other end of edge e, seen from cluster b
 template <bool FIRST_PASS>
@@ -195,8 +190,48 @@ __device__ __forceinline__ int32_t other_end(int32_t e, int32_t b, const int32_t
     return p == b ? q : p;
 }
 
-// LPC lanes per cluster.  The first pass runs over all nodes (every node its
-// own cluster, no cluster-id gather); later passes over the list of heads.
+// Best eligible neighbour over the slots [jb, je) of one member, one thread:
+// eight slots at a time, their suitor keys fetched together (fewer
+// dependent round trips than fetching only for improving slots).
+template <bool D64, bool FIRST_PASS>
+__device__ __forceinline__ void scan_slots_thread(int64_t jb, int64_t je, int32_t cur, const int32_t* __restrict__ col,
+                                                  const int32_t* __restrict__ eid, const uint64_t* __restrict__ keys,
+                                                  const void* __restrict__ d, const int32_t* __restrict__ cl,
+                                                  const void* ws, int32_t* err, typename SK<D64>::K& bk,
+                                                  int32_t& bb) {
+    using T = SK<D64>;
+    constexpr int U = 8;
+    for (int64_t j0 = jb; j0 < je; j0 += U) {
+        int32_t b[U];
+        typename T::K k[U], w[U];
+#pragma unroll
+        for (int t = 0; t < U; ++t) {
+            b[t] = -1;
+            if (j0 + t < je) {
+                const int32_t q = col[j0 + t];
+                b[t] = FIRST_PASS ? q : __ldg(cl + q);
+                if (!FIRST_PASS && b[t] == cur) b[t] = -1;
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < U; ++t) {
+            if (b[t] >= 0) {
+                k[t] = T::slot(j0 + t, eid, keys, d, err);
+                w[t] = T::load(ws, d, b[t]);
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < U; ++t)
+            if (b[t] >= 0 && T::less(k[t], bk) && T::less(k[t], w[t])) {
+                bk = k[t];
+                bb = b[t];
+            }
+    }
+}
+
+// LPC lanes per cluster (1: a thread per cluster).  The first pass runs over
+// all nodes (every node its own cluster, no cluster-id gather); later passes
+// over the list of heads.
 template <bool D64, int LPC, bool FIRST_PASS>
 __global__ void __launch_bounds__(256) k_suitor(
     const int32_t* __restrict__ wl, const int32_t* __restrict__ wl_count, int64_t n,
@@ -205,6 +240,8 @@ __global__ void __launch_bounds__(256) k_suitor(
     const int32_t* __restrict__ nxt, const int32_t* __restrict__ eu, const int32_t* __restrict__ ev, void* ws,
     int64_t chain_cap, unsigned long long* __restrict__ proposals, int32_t* __restrict__ err_key,
     int32_t* __restrict__ err_chain) {
+    using T = SK<D64>;
+    using K = typename T::K;
     const int l = threadIdx.x % LPC;
     const unsigned gmask = LPC == 32 ? 0xffffffffu : (((1u << LPC) - 1u) << ((threadIdx.x & 31) / LPC * LPC));
     const int64_t count = FIRST_PASS ? n : (int64_t)*wl_count;
@@ -214,31 +251,36 @@ __global__ void __launch_bounds__(256) k_suitor(
         int32_t cur = FIRST_PASS ? (int32_t)g : wl[g];
         int64_t steps = 0;
         while (cur >= 0) {
-            Key bk = key_inf();
+            K bk = T::inf();
             int32_t bb = -1;
             for (int32_t p = cur; p >= 0; p = FIRST_PASS ? -1 : nxt[p]) {
                 const int64_t e_end = rowptr[p + 1];
-                for (int64_t j = rowptr[p] + l; j < e_end; j += LPC) {
-                    const int32_t b = FIRST_PASS ? col[j] : __ldg(cl + col[j]);
-                    if (!FIRST_PASS && b == cur) continue;
-                    const Key k = slot_key<D64>(j, eid, keys, d, err_key);
-                    if (!key_less(k, bk)) continue;
-                    if (key_less(k, ws_load<D64>(ws, d, b))) {
-                        bk = k;
-                        bb = b;
+                if constexpr (LPC == 1) {
+                    scan_slots_thread<D64, FIRST_PASS>(rowptr[p], e_end, cur, col, eid, keys, d, cl, ws, err_key, bk,
+                                                       bb);
+                } else {
+                    for (int64_t j = rowptr[p] + l; j < e_end; j += LPC) {
+                        const int32_t b = FIRST_PASS ? col[j] : __ldg(cl + col[j]);
+                        if (!FIRST_PASS && b == cur) continue;
+                        const K k = T::slot(j, eid, keys, d, err_key);
+                        if (!T::less(k, bk)) continue;
+                        if (T::less(k, T::load(ws, d, b))) {
+                            bk = k;
+                            bb = b;
+                        }
                     }
                 }
             }
-            // group minimum; keys of different slots differ, so all lanes agree
+            if constexpr (LPC > 1) {
+                // group minimum; keys of different slots differ, so all lanes agree
 #pragma unroll
-            for (int o = LPC / 2; o > 0; o >>= 1) {
-                Key ok;
-                ok.hi = __shfl_xor_sync(gmask, bk.hi, o, LPC);
-                ok.lo = __shfl_xor_sync(gmask, bk.lo, o, LPC);
-                const int32_t ob = __shfl_xor_sync(gmask, bb, o, LPC);
-                if (key_less(ok, bk)) {
-                    bk = ok;
-                    bb = ob;
+                for (int o = LPC / 2; o > 0; o >>= 1) {
+                    const K ok = T::shfl_xor(gmask, bk, o, LPC);
+                    const int32_t ob = __shfl_xor_sync(gmask, bb, o, LPC);
+                    if (T::less(ok, bk)) {
+                        bk = ok;
+                        bb = ob;
+                    }
                 }
             }
             if (bb < 0) break;  // no eligible neighbour: cur stays unmatched
@@ -248,13 +290,14 @@ __global__ void __launch_bounds__(256) k_suitor(
             }
             int32_t next = -1;
             if (l == 0) {
-                Key old;
-                if (ws_propose<D64>(ws, d, bb, bk, old))
-                    next = key_is_inf(old) ? -1 : other_end<FIRST_PASS>(key_edge<D64>(old), bb, eu, ev, cl);
+                K old;
+                if (T::propose(ws, d, bb, bk, old))
+                    next = T::is_inf(old) ? -1 : other_end<FIRST_PASS>(T::edge(old), bb, eu, ev, cl);
                 else
                     next = cur;  // lost a race: rescan
             }
-            cur = __shfl_sync(gmask, next, 0, LPC);
+            if constexpr (LPC > 1) cur = __shfl_sync(gmask, next, 0, LPC);
+            else cur = next;
         }
         if (l == 0) mine += (unsigned long long)steps;
     }
@@ -286,25 +329,26 @@ __global__ void k_suitor_pairs(const int32_t* __restrict__ wl, const int32_t* __
                                int32_t* __restrict__ pc, int32_t* __restrict__ pb, uint64_t* __restrict__ phi,
                                uint32_t* __restrict__ plo, int32_t* __restrict__ npairs,
                                int32_t* __restrict__ err_mutual) {
+    using T = SK<D64>;
     const int64_t count = FIRST_PASS ? n : (int64_t)*wl_count;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
         const int32_t b = FIRST_PASS ? (int32_t)i : wl[i];
-        const Key k = ws_load<D64>(ws, d, b);
+        const typename T::K k = T::load(ws, d, b);
         int32_t a = -1;
         bool emit = false;
-        if (!key_is_inf(k)) {
-            a = other_end<FIRST_PASS>(key_edge<D64>(k), b, eu, ev, cl);
-            const Key ka = ws_load<D64>(ws, d, a);
-            if (ka.hi != k.hi || ka.lo != k.lo) atomicExch(err_mutual, 1);
+        if (!T::is_inf(k)) {
+            a = other_end<FIRST_PASS>(T::edge(k), b, eu, ev, cl);
+            const typename T::K ka = T::load(ws, d, a);
+            if (T::less(ka, k) || T::less(k, ka)) atomicExch(err_mutual, 1);
             emit = b < a;
         }
         const int32_t s = warp_slot(emit, npairs);
         if (s >= 0) {
             pc[s] = b;
             pb[s] = a;
-            phi[s] = k.hi;
-            plo[s] = k.lo;
+            phi[s] = T::hi(k);
+            plo[s] = T::lo(k);
         }
     }
 }
@@ -389,7 +433,7 @@ static void launch_suitor_lpc(gr_ctx* c, AggState& S, int lpc, int64_t count, co
                               bool first_pass) {
     if (lpc == 32) launch_suitor_pass<D64, 32>(c, S, count, d, chain_cap, first_pass);
     else if (lpc == 8) launch_suitor_pass<D64, 8>(c, S, count, d, chain_cap, first_pass);
-    else launch_suitor_pass<D64, 4>(c, S, count, d, chain_cap, first_pass);
+    else launch_suitor_pass<D64, 1>(c, S, count, d, chain_cap, first_pass);
 }
 
 gr_status aggregate_impl(gr_ctx* c, const void* d, int d_is_f64, int64_t target_nc, int passes,
@@ -438,7 +482,7 @@ gr_status aggregate_impl(gr_ctx* c, const void* d, int d_is_f64, int64_t target_
         count_launch();
     }
     const double avg = n > 0 ? 2.0 * (double)c->m / (double)n : 0.0;
-    const int lpc = avg >= 24 ? 32 : (avg >= 6 ? 8 : 4);
+    const int lpc = avg >= 24 ? 32 : (avg >= 12 ? 8 : 1);
     // a proposal chain can never be longer than the number of suitor-key
     // decreases (at most 2m) plus the failed races; far beyond that is a fault
     const int64_t chain_cap = 4 * c->m + 2 * n + 64;

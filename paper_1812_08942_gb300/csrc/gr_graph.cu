@@ -1,5 +1,7 @@
 // Graph construction: the symmetric CSR of A_G and the degrees D_G (Sec. 2.1),
-// and Galerkin coarsening L_R = P^T L_G P (Sec. 3.2.2) by sort + segmented sum.
+// and Galerkin coarsening L_R = P^T L_G P (Sec. 3.2.2): row by row in shared
+// memory (gr_galerkin.cu), or by a global sort + segmented sum when a coarse
+// row is too long for that.
 #include "gr_internal.cuh"
 
 namespace gr {
@@ -169,18 +171,23 @@ gr_status build_csr(gr_ctx* c) {
         k_fill_upper<<<(unsigned)ceil_div(m, TB), TB, 0, s>>>(c->eu, c->ev, c->ew, m, c->eptr, lcnt,
                                                               c->rowptr, c->col, c->eid, c->wn64); count_launch();
     }
+    GR_TRY_CUDA(c, degree_scale(c), "degree scale");
+    return GR_OK;
+}
+
+cudaError_t degree_scale(gr_ctx* c) {
+    const int64_t n = c->n, m = c->m;
     if (n > 0) {
         if (2 * m < 32 * n) {  // mean degree below 32: a thread per row
-            k_degree_scale_rows<<<(unsigned)ceil_div(n, TB), TB, 0, s>>>(c->rowptr, c->col, n, c->wn64, c->cw32,
-                                                                         c->deg);
+            k_degree_scale_rows<<<(unsigned)ceil_div(n, TB), TB, 0, c->stream>>>(c->rowptr, c->col, n, c->wn64,
+                                                                                 c->cw32, c->deg);
         } else {
-            k_degree_scale<<<(unsigned)ceil_div(n * 32, TB), TB, 0, s>>>(c->rowptr, c->col, n, c->wn64, c->cw32,
-                                                                        c->deg);
+            k_degree_scale<<<(unsigned)ceil_div(n * 32, TB), TB, 0, c->stream>>>(c->rowptr, c->col, n, c->wn64,
+                                                                                c->cw32, c->deg);
         }
         count_launch();
     }
-    GR_TRY_CUDA(c, cudaGetLastError(), "csr kernels");
-    return GR_OK;
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
@@ -251,14 +258,6 @@ gr_status coarsen_impl(gr_ctx* c, const int32_t* agg, int64_t nc, gr_ctx** out) 
     if (!hs) return set_error(c, GR_ENOMEM, "coarsen: pinned scratch unavailable");
     if (nc < 1 || nc > n) return set_error(c, GR_EINVAL, "coarsen: nc must be in [1, n]");
     if ((uint64_t)nc > (1ull << 31)) return set_error(c, GR_EINVAL, "coarsen: nc too large");
-    // labels must lie in [0, nc) and all be used
-    void* p_chk;
-    GR_TRY_CUDA(c, c->ws.get(WS_COARSE_TMP, sizeof(int32_t) * (size_t)(nc + 2), &p_chk), "ws");
-    int32_t* used = (int32_t*)p_chk;
-    int32_t* bad = used + nc;
-    GR_TRY_CUDA(c, cudaMemsetAsync(used, 0, sizeof(int32_t) * (size_t)(nc + 1), s), "memset");
-    k_check_labels<<<(unsigned)ceil_div(n, TB), TB, 0, s>>>(agg, n, nc, used, bad); count_launch();
-    k_check_used<<<(unsigned)ceil_div(nc, TB), TB, 0, s>>>(used, nc, bad); count_launch();
 
     gr_ctx* cc = new gr_ctx();
     cc->stream = s;
@@ -270,6 +269,31 @@ gr_status coarsen_impl(gr_ctx* c, const int32_t* agg, int64_t nc, gr_ctx** out) 
         graph_reduce_destroy(cc);
         return st;
     };
+    // row-by-row assembly unless a coarse row is too long for shared memory
+    bool too_long = false;
+    {
+        gr_status st = galerkin_rows(c, agg, nc, cc, &too_long);
+        if (st != GR_OK) return fail(st);
+        if (!too_long) {
+            if (cudaMallocAsync(&cc->parent_map, sizeof(int32_t) * (size_t)(n > 0 ? n : 1), s) != cudaSuccess) {
+                set_error(c, GR_ENOMEM, "coarsen: allocation failed");
+                return fail(GR_ENOMEM);
+            }
+            GR_TRY_CUDA(c, cudaMemcpyAsync(cc->parent_map, agg, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice,
+                                           s), "copy map");
+            cc->parent_n = n;
+            *out = cc;
+            return GR_OK;
+        }
+    }
+    // global sort path: labels must lie in [0, nc) and all be used
+    void* p_chk;
+    GR_TRY_CUDA(c, c->ws.get(WS_COARSE_TMP, sizeof(int32_t) * (size_t)(nc + 2), &p_chk), "ws");
+    int32_t* used = (int32_t*)p_chk;
+    int32_t* bad = used + nc;
+    GR_TRY_CUDA(c, cudaMemsetAsync(used, 0, sizeof(int32_t) * (size_t)(nc + 1), s), "memset");
+    k_check_labels<<<(unsigned)ceil_div(n, TB), TB, 0, s>>>(agg, n, nc, used, bad); count_launch();
+    k_check_used<<<(unsigned)ceil_div(nc, TB), TB, 0, s>>>(used, nc, bad); count_launch();
     int64_t mc = 0;
     if (m > 0) {
         void *p_k, *p_v, *p_head;

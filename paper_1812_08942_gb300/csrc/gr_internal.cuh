@@ -42,6 +42,7 @@ enum WsSlot {
     WS_SMOOTH_BUF, WS_SMOOTH_STATS, WS_SMOOTH_PART,
     WS_AGG_STATE, WS_AGG_LIST, WS_AGG_KEYS, WS_AGG_SMALL,
     WS_COARSE_KEYS, WS_COARSE_VALS, WS_COARSE_TMP,
+    WS_GAL_KEYS, WS_GAL_UCOL, WS_GAL_UW, WS_GAL_ROWS,
     WS_LOSS_A, WS_LOSS_B, WS_LOSS_C,
     WS_ML_X, WS_ML_D, WS_ML_AGG,
     WS_PINNED_UNUSED,
@@ -106,6 +107,26 @@ uint64_t launch_count();
 
 // graph construction (gr_graph.cu)
 gr_status build_csr(gr_ctx* c);
+// deg = row sums of the raw slot weights in wn64, then wn64 / cw32 scaled by 1 / deg
+cudaError_t degree_scale(gr_ctx* c);
+// Galerkin product assembled row by row (gr_galerkin.cu).  Fills the coarse
+// context cc (n = nc set by the caller) or, when the coarse rows are too long
+// for per-row sorting, sets *too_long and leaves cc untouched.
+gr_status galerkin_rows(gr_ctx* c, const int32_t* agg, int64_t nc, gr_ctx* cc, bool* too_long);
+
+// Slot of the calling lane in a list that grows by one entry per lane with
+// `keep` set: one atomic per warp, entries in lane order; -1 if !keep.
+__device__ __forceinline__ int32_t warp_slot(bool keep, int32_t* count) {
+    const unsigned active = __activemask();
+    const unsigned ball = __ballot_sync(active, keep);
+    if (!ball) return -1;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(ball) - 1;
+    int32_t base = 0;
+    if (lane == leader) base = atomicAdd(count, __popc(ball));
+    base = __shfl_sync(active, base, leader);
+    return keep ? base + __popc(ball & ((1u << lane) - 1u)) : -1;
+}
 
 // kernels entry points used by the API layer
 // ev_begin / ev_end (optional) are recorded around the sweep kernels only

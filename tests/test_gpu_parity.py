@@ -228,6 +228,49 @@ def test_coarsen_parity(gr, oracle_mod, case):
     assert np.array_equal(gr.graph_reduce_get_map(C).cpu().numpy(), agg)
 
 
+def _tier_labels(n, sizes, seed):
+    """Labels of aggregates with the given member counts, members scattered
+    over the node range and labels in a random order."""
+    rng = np.random.default_rng(seed)
+    lab = np.repeat(np.arange(len(sizes)), sizes)[:n]
+    lab = np.concatenate([lab, np.arange(len(sizes), len(sizes) + n - len(lab))])
+    perm = rng.permutation(lab.max() + 1)
+    return perm[rng.permutation(lab)].astype(np.int32)
+
+
+# Coarse rows of up to 128 slots are assembled by the small-row kernel, up to
+# 1,024 by the medium one; longer rows (or many medium ones) send the whole
+# product to the global sort.  Aggregates of 1-3, 40, 600 and 3,000 members of
+# a graph of mean degree ~10 reach each path.
+TIER_CASES = [
+    ("all_medium", [40] * 150),
+    ("small_and_medium", [1] * 3000 + [3] * 900 + [40] * 7),
+    ("global_sort_long", [600] * 10),
+    ("global_sort_many_medium", [3000, 3000]),
+    ("mixed", [1] * 500 + [3] * 300 + [40] * 60 + [600] * 4 + [2000]),
+]
+
+
+@pytest.mark.parametrize("case", TIER_CASES, ids=[c[0] for c in TIER_CASES])
+def test_coarsen_row_tiers(gr, oracle_mod, case):
+    _, sizes = case
+    g = W.random_sparse(6000, 30000, seed=21)
+    agg = _tier_labels(g.n, sizes, seed=3)
+    nc = int(agg.max()) + 1
+    uc, vc, wc = oracle_mod.coarsen(g.n, g.u, g.v, g.w, agg, nc)
+    G = gr.graph_reduce_create(g.n, g.u, g.v, g.w)
+    C = gr.graph_reduce_coarsen(G, torch.from_numpy(agg).to(DEV), nc)
+    assert C.n == nc and C.m == len(uc)
+    gu, gv, gw = (t.numpy() for t in gr.graph_reduce_get_edges(C, on_host=True))
+    assert np.array_equal(gu, uc) and np.array_equal(gv, vc) and np.array_equal(gw, wc)
+    # the coarse CSR and degrees, through a smoothing run on the coarse graph
+    K, S = 8, 3
+    ref = oracle_mod.smooth(nc, uc, vc, wc, K, S, 0.7, 5, 1)
+    X = torch.empty(nc, K, dtype=torch.float64, device=DEV)
+    gr.graph_reduce_smooth(C, X, S, 0.7, 5, 1)
+    assert _col_relerr(X.cpu().numpy(), ref).max() <= 1e-12
+
+
 def test_coarsen_rejects_bad_labels(gr):
     g = W.grid2d(8, 8)
     G = gr.graph_reduce_create(g.n, g.u, g.v, g.w)
