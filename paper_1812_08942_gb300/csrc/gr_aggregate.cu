@@ -200,7 +200,7 @@ __device__ __forceinline__ void scan_slots_thread(int64_t jb, int64_t je, int32_
                                                   const void* ws, int32_t* err, typename SK<D64>::K& bk,
                                                   int32_t& bb) {
     using T = SK<D64>;
-    constexpr int U = 8;
+    constexpr int U = 4;
     for (int64_t j0 = jb; j0 < je; j0 += U) {
         int32_t b[U];
         typename T::K k[U], w[U];

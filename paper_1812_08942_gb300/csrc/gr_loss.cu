@@ -62,9 +62,17 @@ __global__ void k_finish_sums(const double* __restrict__ part, int nblocks, int 
                               double* __restrict__ out) {
     int j = threadIdx.x;
     if (j >= NS) return;
-    double s = 0.0;
-    for (int b = 0; b < nblocks; ++b) s += part[(int64_t)b * NS + j];
-    out[j] = s;
+    // eight interleaved accumulators keep eight loads in flight (fixed order)
+    double a[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) a[u] = 0.0;
+    int b = 0;
+    for (; b + 7 < nblocks; b += 8) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) a[u] += part[(int64_t)(b + u) * NS + j];
+    }
+    for (; b < nblocks; ++b) a[0] += part[(int64_t)b * NS + j];
+    out[j] = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
 }
 
 // sum_e w_e (x_u - x_v)^2 per column, over a canonical edge list

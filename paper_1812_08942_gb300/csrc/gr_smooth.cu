@@ -31,9 +31,21 @@ __device__ void finish_stats(const double* __restrict__ part, int nblocks, int64
     const int t = threadIdx.x;
     const int stat = t % NS;
     const int sub = t / NS;
+    // eight interleaved accumulators keep eight loads in flight; the order of
+    // the additions depends only on nblocks, so results are reproducible
     double acc = 0.0;
-    if (sub < PER)
-        for (int b = sub; b < nblocks; b += PER) acc += __ldcg(part + (int64_t)b * NS + stat);
+    if (sub < PER) {
+        double a[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) a[u] = 0.0;
+        int b = sub;
+        for (; b + 7 * PER < nblocks; b += 8 * PER) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) a[u] += __ldcg(part + (int64_t)(b + u * PER) * NS + stat);
+        }
+        for (; b < nblocks; b += PER) a[0] += __ldcg(part + (int64_t)b * NS + stat);
+        acc = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+    }
     red[t] = acc;
     __syncthreads();
     if (t < NS) {
@@ -580,25 +592,35 @@ __global__ void __launch_bounds__(SM_THREADS) k_sweep_row(
     block_stats_rows<Acc, K, E, G>(s1, s2, part, counter, n64, stats_out);
 }
 
-// X = (A - mu) * inv_s, chunk-parallel
+// X = (A - mu) * inv_s, chunk-parallel.  The statistics are converted to the
+// accumulator type once per block; chunk indices are 32-bit when they fit.
 template <typename T, int K>
 __global__ void k_apply(int64_t n, const T* __restrict__ A, T* __restrict__ X,
                         const double* __restrict__ stats) {
     using L = RowLayout<T, K>;
     using Acc = typename AccOf<T>::type;
     constexpr int E = L::E, G = L::G;
-    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= n * G) return;
-    int64_t row = idx / G;
-    int q = (int)(idx % G);
-    Acc x[E];
-    load_chunk<T, E>(A + row * K + q * E, x);
+    __shared__ Acc st[2 * K];
+    for (int i = threadIdx.x; i < 2 * K; i += blockDim.x) st[i] = (Acc)stats[i];
+    __syncthreads();
+    const uint64_t total = (uint64_t)n * G;
+    auto one = [&](int64_t row, int q) {
+        Acc x[E];
+        load_chunk<T, E>(A + row * K + q * E, x);
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-        int k = q * E + e;
-        x[e] = (x[e] - (Acc)stats[k]) * (Acc)stats[K + k];
+        for (int e = 0; e < E; ++e) {
+            const int k = q * E + e;
+            x[e] = (x[e] - st[k]) * st[K + k];
+        }
+        store_chunk<T, E>(X + row * K + q * E, x);
+    };
+    if (total <= 0xffffffffull) {
+        const uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x;
+        if (idx < (uint32_t)total) one((int64_t)(idx / G), (int)(idx % G));
+    } else {
+        const uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        if (idx < total) one((int64_t)(idx / G), (int)(idx % G));
     }
-    store_chunk<T, E>(X + row * K + q * E, x);
 }
 
 // ---------------------------------------------------------------------------
