@@ -50,19 +50,6 @@ static bool host_canonical(int64_t n, int64_t m, const int32_t* u, const int32_t
     return true;
 }
 
-__global__ void k_canonical_check(int64_t n, int64_t m, const int32_t* __restrict__ u,
-                                  const int32_t* __restrict__ v, const double* __restrict__ w,
-                                  int32_t* __restrict__ bad) {
-    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= m) return;
-    int32_t a = u[e], b = v[e];
-    bool ok = a >= 0 && b < n && a < b && w[e] > 0.0 && isfinite(w[e]);
-    if (e > 0) {
-        int32_t pa = u[e - 1], pb = v[e - 1];
-        ok = ok && (pa < a || (pa == a && pb < b));
-    }
-    if (!ok) atomicExch(bad, 1);
-}
 
 }  // namespace gr
 
@@ -101,32 +88,18 @@ gr_status graph_reduce_create(gr_ctx** out, int64_t n, int64_t m, const int32_t*
         graph_reduce_destroy(c);
         return e == cudaErrorMemoryAllocation ? GR_ENOMEM : GR_ECUDA;
     }
-    if (m > 0) {  // host or device inputs: checked on the device after the copy
-        int32_t* bad = (int32_t*)(hs + 4);
-        *bad = 0;
-        void* dbad;
-        e = c->ws.get(WS_COARSE_TMP, 16, &dbad);
-        if (e == cudaSuccess) e = cudaMemsetAsync(dbad, 0, 4, c->stream);
-        if (e == cudaSuccess) {
-            k_canonical_check<<<(unsigned)ceil_div(m, 256), 256, 0, c->stream>>>(n, m, c->eu, c->ev, c->ew,
-                                                                                (int32_t*)dbad); count_launch();
-            e = cudaMemcpyAsync(bad, dbad, 4, cudaMemcpyDeviceToHost, c->stream);
-        }
-        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-        if (e != cudaSuccess || *bad) {
-            if (e != cudaSuccess) cuda_error(nullptr, e, "create");
-            else {
-                std::string why = "the edge list is not canonical (u < v < n, sorted, unique, w > 0 finite)";
-                if (inputs_on_host) host_canonical(n, m, u, v, w, &why);  // name the first bad edge
-                set_error(nullptr, GR_EINVAL, "create: " + why);
-            }
-            graph_reduce_destroy(c);
-            return e != cudaSuccess ? GR_ECUDA : GR_EINVAL;
-        }
-    }
-    gr_status st = build_csr(c);
+    // host or device inputs: checked on the device after the copy, in the
+    // first pass of the CSR build
+    bool invalid = false;
+    gr_status st = build_csr(c, true, &invalid);
     if (st != GR_OK) {
-        set_error(nullptr, st, c->last_error);
+        if (invalid) {
+            std::string why = "the edge list is not canonical (u < v < n, sorted, unique, w > 0 finite)";
+            if (inputs_on_host) host_canonical(n, m, u, v, w, &why);  // name the first bad edge
+            set_error(nullptr, GR_EINVAL, "create: " + why);
+        } else {
+            set_error(nullptr, st, c->last_error);
+        }
         graph_reduce_destroy(c);
         return st;
     }

@@ -21,11 +21,6 @@ __global__ void k_upper_ptr(const int32_t* __restrict__ eu, int64_t m, int64_t n
     for (int64_t p = prev + 1; p <= cur; ++p) eptr[p] = e;
 }
 
-__global__ void k_lower_count(const int32_t* __restrict__ ev, int64_t m, int32_t* __restrict__ lcnt) {
-    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e < m) atomicAdd(&lcnt[ev[e]], 1);
-}
-
 // rowcnt[p] = lower count + upper count (entry n is 0); lc64 = lower count as int64
 __global__ void k_row_count(const int32_t* __restrict__ lcnt, const int64_t* __restrict__ eptr,
                             int64_t n, int64_t* __restrict__ rowcnt, int64_t* __restrict__ lc64) {
@@ -121,9 +116,184 @@ __global__ void k_degree_scale_rows(const int64_t* __restrict__ rowptr, const in
     }
 }
 
-gr_status build_csr(gr_ctx* c) {
+// ---------------------------------------------------------------------------
+// CSR of a sparse graph by lower-part sorting.  The upper part of row p
+// (edges (p, v), v > p) is a contiguous, sorted run of the canonical list; the
+// lower part (edges (q, p), q < p) is gathered by atomic slot claims and then
+// sorted per row by edge id, which for a fixed p is ascending q.  One pass per
+// row then writes both parts, the degree and the row-scaled weights.
+// ---------------------------------------------------------------------------
+constexpr int LOWER_THREAD = 32;   // lower parts up to this long: sorted by the row's own thread
+constexpr int LOWER_WARP = 2048;   // up to this long: by a warp in shared memory; longer: global sort
+constexpr int FW = 4;              // warps per block of the warp kernel
+
+// per edge: canonical-input check (when asked) and the lower count of v;
+// the block maximum of the counts reached goes to lmax
+__global__ void k_csr_count(int64_t n, int64_t m, const int32_t* __restrict__ u, const int32_t* __restrict__ v,
+                            const double* __restrict__ w, int check, int32_t* __restrict__ lcnt,
+                            int32_t* __restrict__ bad, int32_t* __restrict__ lmax) {
+    __shared__ int32_t bmax;
+    if (threadIdx.x == 0) bmax = 0;
+    __syncthreads();
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < m) {
+        const int32_t a = u[e], b = v[e];
+        if (check) {
+            bool ok = a >= 0 && b < n && a < b && w[e] > 0.0 && isfinite(w[e]);
+            if (e > 0) {
+                const int32_t pa = u[e - 1], pb = v[e - 1];
+                ok = ok && (pa < a || (pa == a && pb < b));
+            }
+            if (!ok) atomicExch(bad, 1);
+        }
+        if (b >= 0 && b < n) atomicMax(&bmax, atomicAdd(&lcnt[b], 1) + 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && bmax) atomicMax(lmax, bmax);
+}
+
+__global__ void k_row_total(const int32_t* __restrict__ lcnt, const int64_t* __restrict__ eptr, int64_t n,
+                            int64_t* __restrict__ rowcnt) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < n) rowcnt[p] = (int64_t)lcnt[p] + (eptr[p + 1] - eptr[p]);
+    else if (p == n) rowcnt[p] = 0;
+}
+
+// lower part of row v: edge ids in claim order (sorted by the row pass)
+__global__ void k_lower_claim(const int32_t* __restrict__ ev, int64_t m, const int64_t* __restrict__ rowptr,
+                              int32_t* __restrict__ lfill, int32_t* __restrict__ eid) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m) return;
+    const int32_t b = ev[e];
+    eid[rowptr[b] + atomicAdd(&lfill[b], 1)] = (int32_t)e;
+}
+
+// thread per row (graphs of mean degree below 32): insertion-sort the lower ids, write
+// the row, D(p,p) summed sequentially in slot order (= ascending edge id),
+// then w / D(p,p).  Rows with longer lower parts go to the warp kernel's list.
+__global__ void k_row_finish_thread(int64_t n, const int64_t* __restrict__ rowptr, const int64_t* __restrict__ eptr,
+                                    const int32_t* __restrict__ lcnt, const int32_t* __restrict__ eu,
+                                    const int32_t* __restrict__ ev, const double* __restrict__ ew,
+                                    int32_t* __restrict__ col, int32_t* __restrict__ eid,
+                                    double* __restrict__ wn64, int2* __restrict__ cw32, double* __restrict__ deg,
+                                    int32_t* __restrict__ list, int32_t* __restrict__ nlist) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int L = lcnt[p];
+    const int32_t k = warp_slot(L > LOWER_THREAD, nlist);
+    if (k >= 0) {
+        list[k] = (int32_t)p;
+        return;
+    }
+    const int64_t r0 = rowptr[p], e0 = eptr[p], e1 = eptr[p + 1];
+    int32_t le[LOWER_THREAD];
+    for (int i = 0; i < L; ++i) {
+        const int32_t x = eid[r0 + i];
+        int j = i;
+        while (j > 0 && le[j - 1] > x) {
+            le[j] = le[j - 1];
+            --j;
+        }
+        le[j] = x;
+    }
+    double sum = 0.0;
+    for (int i = 0; i < L; ++i) {
+        const int32_t e = le[i];
+        const double w = ew[e];
+        col[r0 + i] = eu[e];
+        eid[r0 + i] = e;
+        wn64[r0 + i] = w;
+        sum += w;
+    }
+    for (int64_t e = e0; e < e1; ++e) {
+        const int64_t j = r0 + L + (e - e0);
+        const double w = ew[e];
+        col[j] = ev[e];
+        eid[j] = (int32_t)e;
+        wn64[j] = w;
+        sum += w;
+    }
+    deg[p] = sum;
+    const double inv = sum > 0.0 ? 1.0 / sum : 0.0;
+    const int64_t r1 = r0 + L + (e1 - e0);
+    for (int64_t j = r0; j < r1; ++j) {
+        const double x = wn64[j] * inv;
+        wn64[j] = x;
+        cw32[j] = make_int2(col[j], __float_as_int((float)x));
+    }
+}
+
+// warp per listed row (lower part longer than a thread sorts): lower ids
+// bitonic-sorted in shared memory; D(p,p) as lane-strided sums in slot order
+// combined by a fixed shuffle tree
+__global__ void __launch_bounds__(FW * 32) k_row_finish_warp(
+    const int32_t* __restrict__ list, const int32_t* __restrict__ nlist,
+    const int64_t* __restrict__ rowptr, const int64_t* __restrict__ eptr, const int32_t* __restrict__ lcnt,
+    const int32_t* __restrict__ eu, const int32_t* __restrict__ ev, const double* __restrict__ ew,
+    int32_t* __restrict__ col, int32_t* __restrict__ eid, double* __restrict__ wn64, int2* __restrict__ cw32,
+    double* __restrict__ deg) {
+    __shared__ int32_t sh[FW][LOWER_WARP];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int32_t* S = sh[w];
+    const int64_t count = *nlist;
+    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < count;
+         r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int64_t p = list[r];
+        const int L = lcnt[p];
+        const int64_t r0 = rowptr[p], e0 = eptr[p], e1 = eptr[p + 1];
+        const int P = L <= 1 ? 1 : 1 << (32 - __clz(L - 1));
+        for (int t = lane; t < P; t += 32) S[t] = t < L ? eid[r0 + t] : 0x7fffffff;
+        __syncwarp();
+        for (int kk = 2; kk <= P; kk <<= 1)
+            for (int j = kk >> 1; j > 0; j >>= 1) {
+                for (int t = lane; t < P; t += 32) {
+                    const int u2 = t ^ j;
+                    if (u2 > t) {
+                        const int32_t x = S[t], y = S[u2];
+                        if ((x > y) == ((t & kk) == 0)) {
+                            S[t] = y;
+                            S[u2] = x;
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+        const int64_t len = L + (e1 - e0);
+        double sum = 0.0;
+        for (int64_t i = lane; i < len; i += 32) {
+            int32_t e, q;
+            if (i < L) {
+                e = S[i];
+                q = eu[e];
+            } else {
+                e = (int32_t)(e0 + (i - L));
+                q = ev[e];
+            }
+            const double wv = ew[e];
+            col[r0 + i] = q;
+            eid[r0 + i] = e;
+            wn64[r0 + i] = wv;
+            sum += wv;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if (lane == 0) deg[p] = sum;
+        const double inv = sum > 0.0 ? 1.0 / sum : 0.0;
+        for (int64_t i = lane; i < len; i += 32) {
+            const double x = wn64[r0 + i] * inv;
+            wn64[r0 + i] = x;
+            cw32[r0 + i] = make_int2(col[r0 + i], __float_as_int((float)x));
+        }
+        __syncwarp();
+    }
+}
+
+gr_status build_csr(gr_ctx* c, bool check, bool* invalid) {
     const int64_t n = c->n, m = c->m;
     cudaStream_t s = c->stream;
+    if (invalid) *invalid = false;
+    int64_t* hs = host_scratch();
+    if (!hs) return set_error(c, GR_ENOMEM, "csr: pinned scratch unavailable");
     GR_TRY_CUDA(c, cudaMallocAsync(&c->eptr, sizeof(int64_t) * (n + 1), s), "alloc eptr");
     GR_TRY_CUDA(c, cudaMallocAsync(&c->rowptr, sizeof(int64_t) * (n + 1), s), "alloc rowptr");
     GR_TRY_CUDA(c, cudaMallocAsync(&c->deg, sizeof(double) * (n > 0 ? n : 1), s), "alloc deg");
@@ -133,25 +303,73 @@ gr_status build_csr(gr_ctx* c) {
     GR_TRY_CUDA(c, cudaMallocAsync(&c->cw32, sizeof(int2) * slots, s), "alloc cw32");
     GR_TRY_CUDA(c, cudaMallocAsync(&c->wn64, sizeof(double) * slots, s), "alloc wn64");
 
-    void *p_lcnt, *p_i64;
-    GR_TRY_CUDA(c, c->ws.get(WS_COARSE_TMP, sizeof(int32_t) * (size_t)(n + 1), &p_lcnt), "ws");
-    GR_TRY_CUDA(c, c->ws.get(WS_SORT_C, sizeof(int64_t) * (size_t)(n + 1) * 3, &p_i64), "ws");
-    int32_t* lcnt = (int32_t*)p_lcnt;
+    // lcnt (n+1), lfill (n+1), list (n+1), flags (16 B); rowcnt (n+1, int64)
+    void *p_i32, *p_i64;
+    const size_t R = (size_t)(n + 1);
+    GR_TRY_CUDA(c, c->ws.get(WS_COARSE_TMP, sizeof(int32_t) * (3 * R + 4), &p_i32), "ws");
+    GR_TRY_CUDA(c, c->ws.get(WS_SORT_C, sizeof(int64_t) * R * 3, &p_i64), "ws");
+    int32_t* lcnt = (int32_t*)p_i32;
+    int32_t* lfill = lcnt + R;
+    int32_t* list = lfill + R;
+    int32_t* flags = list + R;  // [0] not canonical, [1] longest lower part, [2] listed rows
     int64_t* rowcnt = (int64_t*)p_i64;
-    int64_t* lc64 = rowcnt + (n + 1);
-    int64_t* lstart = lc64 + (n + 1);
 
-    k_upper_ptr<<<(unsigned)ceil_div(m + 1, TB), TB, 0, s>>>(c->eu, m, n, c->eptr); count_launch();
-    GR_TRY_CUDA(c, cudaMemsetAsync(lcnt, 0, sizeof(int32_t) * (size_t)(n + 1), s), "memset");
+    GR_TRY_CUDA(c, cudaMemsetAsync(lcnt, 0, sizeof(int32_t) * (2 * R), s), "memset");
+    GR_TRY_CUDA(c, cudaMemsetAsync(flags, 0, 16, s), "memset");
     if (m > 0) {
-        k_lower_count<<<(unsigned)ceil_div(m, TB), TB, 0, s>>>(c->ev, m, lcnt);
+        k_csr_count<<<(unsigned)ceil_div(m, TB), TB, 0, s>>>(n, m, c->eu, c->ev, c->ew, check ? 1 : 0, lcnt, flags,
+                                                            flags + 1);
         count_launch();
     }
+    // dense graphs (mean degree 32 or more): the global sort of the lower
+    // parts beats per-row sorting of long lower parts
+    const bool sparse = 2 * m < 32 * n;
+    int32_t lmax = 0;
+    if (check || sparse) {
+        GR_TRY_CUDA(c, cudaMemcpyAsync(hs, flags, 16, cudaMemcpyDeviceToHost, s), "readback");
+        GR_TRY_CUDA(c, cudaStreamSynchronize(s), "sync");
+        const int32_t* hf = (const int32_t*)hs;
+        if (hf[0]) {
+            if (invalid) *invalid = true;
+            return set_error(c, GR_EINVAL, "csr: the edge list is not canonical");
+        }
+        lmax = hf[1];
+    }
+    k_upper_ptr<<<(unsigned)ceil_div(m + 1, TB), TB, 0, s>>>(c->eu, m, n, c->eptr); count_launch();
+    if (!sparse || lmax > LOWER_WARP) return build_csr_sorted(c, lcnt, rowcnt);
+    k_row_total<<<(unsigned)ceil_div(n + 1, TB), TB, 0, s>>>(lcnt, c->eptr, n, rowcnt); count_launch();
+    GR_TRY_CUDA(c, scan_exclusive_i64(rowcnt, c->rowptr, n + 1, c->ws, s), "scan rowptr");
+    if (m > 0) {
+        k_lower_claim<<<(unsigned)ceil_div(m, TB), TB, 0, s>>>(c->ev, m, c->rowptr, lfill, c->eid);
+        count_launch();
+    }
+    if (n > 0) {
+        k_row_finish_thread<<<(unsigned)ceil_div(n, TB), TB, 0, s>>>(n, c->rowptr, c->eptr, lcnt, c->eu, c->ev,
+                                                                   c->ew, c->col, c->eid, c->wn64, c->cw32, c->deg,
+                                                                   list, flags + 2);
+        count_launch();
+        if (lmax > LOWER_THREAD) {
+            k_row_finish_warp<<<(unsigned)(c->num_sms * 16), FW * 32, 0, s>>>(list, flags + 2, c->rowptr, c->eptr,
+                                                                              lcnt, c->eu, c->ev, c->ew, c->col,
+                                                                              c->eid, c->wn64, c->cw32, c->deg);
+            count_launch();
+        }
+    }
+    GR_TRY_CUDA(c, cudaGetLastError(), "csr kernels");
+    return GR_OK;
+}
+
+// Rows with a lower part too long for one warp's shared memory: a stable
+// radix sort of the edge ids by v lists every row's lower part in order.
+gr_status build_csr_sorted(gr_ctx* c, const int32_t* lcnt, int64_t* rowcnt) {
+    const int64_t n = c->n, m = c->m;
+    cudaStream_t s = c->stream;
+    int64_t* lc64 = rowcnt + (n + 1);
+    int64_t* lstart = lc64 + (n + 1);
     k_row_count<<<(unsigned)ceil_div(n + 1, TB), TB, 0, s>>>(lcnt, c->eptr, n, rowcnt, lc64); count_launch();
     GR_TRY_CUDA(c, scan_exclusive_i64(rowcnt, c->rowptr, n + 1, c->ws, s), "scan rowptr");
     GR_TRY_CUDA(c, scan_exclusive_i64(lc64, lstart, n + 1, c->ws, s), "scan lstart");
     if (m > 0) {
-        // a stable sort of edge ids by v lists every row's lower part in order
         void *p_k0, *p_v0, *p_alt;
         GR_TRY_CUDA(c, c->ws.get(WS_SORT_A, sizeof(uint32_t) * (size_t)m, &p_k0), "ws");
         GR_TRY_CUDA(c, c->ws.get(WS_SORT_B, sizeof(uint32_t) * (size_t)m, &p_v0), "ws");
@@ -349,7 +567,7 @@ gr_status coarsen_impl(gr_ctx* c, const int32_t* agg, int64_t nc, gr_ctx** out) 
         cudaMallocAsync(&cc->ev, 4, s);
         cudaMallocAsync(&cc->ew, 8, s);
     }
-    gr_status st = build_csr(cc);
+    gr_status st = build_csr(cc, false, nullptr);
     if (st != GR_OK) {
         set_error(c, st, "coarsen: " + cc->last_error);
         return fail(st);

@@ -105,8 +105,10 @@ void tune_mempool(int device);
 void count_launch();
 uint64_t launch_count();
 
-// graph construction (gr_graph.cu)
-gr_status build_csr(gr_ctx* c);
+// graph construction (gr_graph.cu).  build_csr checks that the edge list is
+// canonical when `check` is set (*invalid reports a failed check, GR_EINVAL).
+gr_status build_csr(gr_ctx* c, bool check, bool* invalid);
+gr_status build_csr_sorted(gr_ctx* c, const int32_t* lcnt, int64_t* rowcnt);
 // deg = row sums of the raw slot weights in wn64, then wn64 / cw32 scaled by 1 / deg
 cudaError_t degree_scale(gr_ctx* c);
 // Galerkin product assembled row by row (gr_galerkin.cu).  Fills the coarse

@@ -76,6 +76,38 @@ def test_create_roundtrip_and_validation(gr, oracle_mod):
             assert ei.value.status == 1
 
 
+def _star_last(n, seed):
+    """Star whose centre is the last node: its lower part holds n - 1 edges."""
+    rng = np.random.default_rng(seed)
+    return W.Graph(n, np.arange(0, n - 1, dtype=np.int32), np.full(n - 1, n - 1, np.int32),
+                   rng.uniform(0.5, 2.0, n - 1))
+
+
+# The CSR build of a sparse graph sorts each row's lower part by the row's own
+# thread (up to 32 entries) or by a warp (up to 2,048); past that, and for
+# graphs of mean degree 32 or more, a global radix sort lists the lower parts.
+@pytest.mark.parametrize("case", [("thread_to_warp", lambda: _star_last(40, 1)),
+                                  ("warp", lambda: _star_last(1500, 2)),
+                                  ("global_sort", lambda: _star_last(3000, 3)),
+                                  ("dense_global_sort", lambda: W.random_sparse(700, 16000, seed=8))],
+                         ids=lambda c: c[0])
+def test_csr_lower_part_paths(gr, oracle_mod, case):
+    g = case[1]()
+    G = gr.graph_reduce_create(g.n, g.u, g.v, g.w)
+    gu, gv, gw = (t.numpy() for t in gr.graph_reduce_get_edges(G, on_host=True))
+    assert np.array_equal(gu, g.u) and np.array_equal(gv, g.v) and np.array_equal(gw, g.w)
+    K, S = 8, 3
+    ref = oracle_mod.smooth(g.n, g.u, g.v, g.w, K, S, 0.7, 2, 0)
+    X = torch.empty(g.n, K, dtype=torch.float64, device=DEV)
+    gr.graph_reduce_smooth(G, X, S, 0.7, 2, 0)
+    assert _col_relerr(X.cpu().numpy(), ref).max() <= 1e-12
+    # and the FP64 distances of every edge from that block, bit-exact
+    d = torch.empty(g.m, dtype=torch.float64, device=DEV)
+    gr.graph_reduce_affinity(G, X, d)
+    dref = oracle_mod.affinity(g.n, g.u, g.v, X.cpu().numpy())
+    assert np.array_equal(d.cpu().numpy(), dref)
+
+
 # ---------------------------------------------------------------------------
 # smoothing
 # ---------------------------------------------------------------------------
