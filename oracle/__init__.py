@@ -59,6 +59,7 @@ def _load():
         "oracle_aggregate": (I, [I64, I64, P, P, P, I64, I, P, P, P]),
         "oracle_coarsen": (I, [I64, I64, P, P, P, P, I64, P, P, P, P]),
         "oracle_loss": (I, [I64, I64, P, P, P, I64, I64, P, P, P, P, I, P, I, D, P, P, P, P]),
+        "oracle_shifted_jacobi": (I, [I64, I64, P, P, P, I, P, I, D, I, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -254,6 +255,66 @@ def compose_maps(levels):
     for lv in levels[1:]:
         out = lv.agg[out].astype(np.int64)
     return out.astype(np.int32)
+
+
+# --------------------------------------------------------------------------
+# Multilevel Laplacian eigensolver (Alg. 5, Sec. 4.1; Eqs. equ:lgl, equ:lgs)
+# --------------------------------------------------------------------------
+def shifted_jacobi(n, u, v, w, Y, lam, normalized=False, omega=0.7, iters=10):
+    """`iters` weighted-Jacobi iterations on (L - lam_k B) y = 0 for every
+    column k of Y (n x K), B = I or D (oracle_shifted_jacobi)."""
+    Y = np.array(Y, dtype=np.float64, order="C", copy=True)
+    K = Y.shape[1]
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    assert lam.shape == (K,)
+    lib = _load()
+    u, v, w = _i32(u), _i32(v), _f64(w)
+    _check(lib.oracle_shifted_jacobi(n, len(u), _p(u), _p(v), _p(w), K, _p(lam), 1 if normalized else 0,
+                                     float(omega), int(iters), _p(Y)), "shifted_jacobi")
+    return Y
+
+
+def coarsest_eigenpairs(n, u, v, w, k, normalized=False):
+    """First k eigenpairs (ascending) of L u = lam B u on the coarsest graph
+    (Alg. 5, step 2) by a dense symmetric eigensolver.  B = D is reduced to
+    the standard problem D^-1/2 L D^-1/2 z = lam z, u = D^-1/2 z; a node of
+    degree 0 takes B(i,i) = 1 there (the paper is silent)."""
+    L = dense_laplacian(n, u, v, w)
+    if normalized:
+        b = degrees(n, u, v, w).copy()
+        b[b <= 0.0] = 1.0
+        s = 1.0 / np.sqrt(b)
+        lam, Z = np.linalg.eigh(s[:, None] * L * s[None, :])
+        U = s[:, None] * Z
+    else:
+        lam, U = np.linalg.eigh(L)
+    return lam[:k].copy(), np.ascontiguousarray(U[:, :k])
+
+
+def gram_schmidt(U):
+    """Modified Gram-Schmidt over the columns of U, in column order."""
+    U = np.array(U, dtype=np.float64, copy=True)
+    for i in range(U.shape[1]):
+        for j in range(i):
+            U[:, i] -= (U[:, j] @ U[:, i]) * U[:, j]
+        U[:, i] /= np.sqrt(U[:, i] @ U[:, i])
+    return U
+
+
+def multilevel_eigensolve(graphs, maps, k, normalized=False, omega=0.7, iters=10):
+    """Alg. 5.  graphs[0] is the finest graph (n, u, v, w) and graphs[l] the
+    graph coarsened from graphs[l-1] with aggregate map maps[l-1] (length
+    n_{l-1}).  Coarsest eigenpairs, then for each finer level: map the block
+    with H = P (U_fine[i] = U_coarse[map[i]]) and smooth every column with
+    the coarsest eigenvalue as shift; orthonormalise at the finest level.
+    Returns (U, lam) with lam the coarsest eigenvalues."""
+    assert len(maps) == len(graphs) - 1
+    lam, U = coarsest_eigenpairs(*graphs[-1], k, normalized)
+    for j in range(len(graphs) - 2, -1, -1):
+        U = U[np.asarray(maps[j], np.int64)]
+        n, u, v, w = graphs[j]
+        U = shifted_jacobi(n, u, v, w, U, lam, normalized, omega, iters)
+    return gram_schmidt(U), lam
 
 
 # --------------------------------------------------------------------------

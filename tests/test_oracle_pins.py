@@ -535,3 +535,136 @@ def test_golden_grid64(oracle_mod):
     assert nc == ref["nc"] and len(uc) == ref["mc"]
     assert hashlib.sha256(agg.tobytes()).hexdigest() == ref["agg_sha256"]
     assert float(wc.sum()) == ref["wc_sum"]
+
+
+# ---------------------------------------------------------------------------
+# Multilevel eigensolver (Alg. 5): shifted Jacobi, coarsest eigenpairs,
+# Gram-Schmidt, the level loop
+# ---------------------------------------------------------------------------
+def _cycle_weighted(n, wt):
+    u = np.arange(n - 1, dtype=np.int32)
+    v = np.arange(1, n, dtype=np.int32)
+    u = np.concatenate([np.array([0], np.int32), u])
+    v = np.concatenate([np.array([n - 1], np.int32), v])
+    order = np.lexsort((v, u))
+    return W.Graph(n, u[order], v[order], np.full(n, wt))
+
+
+@pytest.mark.parametrize("normalized", [False, True])
+def test_shifted_jacobi_fixed_point_on_cycle_eigenvectors(oracle_mod, normalized):
+    # unit-free closed form: on a cycle of weight c, L cos(2 pi j i / n) =
+    # 2c (1 - cos(2 pi j / n)) cos(...), D = 2c I; an exact eigenpair of
+    # (L, B) is a fixed point of every shifted Jacobi iteration
+    n, c = 24, 1.5
+    g = _cycle_weighted(n, c)
+    i = np.arange(n)
+    js = [1, 2, 5]
+    Y = np.stack([np.cos(2 * np.pi * j * i / n) for j in js], 1)
+    lam = np.array([2 * c * (1 - np.cos(2 * np.pi * j / n)) for j in js])
+    if normalized:
+        lam = lam / (2 * c)
+    out = oracle_mod.shifted_jacobi(n, g.u, g.v, g.w, Y, lam, normalized, 0.7, 5)
+    assert np.max(np.abs(out - Y)) <= 1e-12
+    # a wrong shift moves the vector (the check above is not vacuous)
+    moved = oracle_mod.shifted_jacobi(n, g.u, g.v, g.w, Y, lam * 0.5, normalized, 0.7, 1)
+    assert np.max(np.abs(moved - Y)) > 1e-3
+
+
+@pytest.mark.parametrize("normalized", [False, True])
+def test_shifted_jacobi_fixed_point_generalized(oracle_mod, normalized):
+    from scipy.linalg import eigh
+    g = W.random_sparse(40, 150, seed=11)
+    L = oracle_mod.dense_laplacian(g.n, g.u, g.v, g.w)
+    B = np.diag(np.diag(L)) if normalized else np.eye(g.n)
+    lam, U = eigh(L, B)  # LAPACK's generalized solver, not the oracle's reduction
+    k = [1, 2, 3, 7]
+    out = oracle_mod.shifted_jacobi(g.n, g.u, g.v, g.w, U[:, k], lam[k], normalized, 0.7, 4)
+    assert np.max(np.abs(out - U[:, k])) <= 1e-10
+
+
+def test_shifted_jacobi_keeps_rows_with_nonpositive_diagonal(oracle_mod):
+    # node 5 is isolated; node 0 has degree 0.2 < shift 0.5 (ratio cut)
+    u = np.array([0, 1, 2, 3], np.int32)
+    v = np.array([1, 2, 3, 4], np.int32)
+    w = np.array([0.2, 1.0, 1.0, 1.0])
+    Y = np.arange(12, dtype=np.float64).reshape(6, 2) + 1.0
+    out = oracle_mod.shifted_jacobi(6, u, v, w, Y, np.array([0.5, 0.0]), False, 0.7, 1)
+    assert out[5, 0] == Y[5, 0] and out[5, 1] == Y[5, 1]
+    assert out[0, 0] == Y[0, 0]  # 0.2 - 0.5 <= 0
+    # node 0, column 1 (shift 0): the plain Alg. 3 update toward its neighbour
+    assert np.isclose(out[0, 1], 0.3 * Y[0, 1] + 0.7 * Y[1, 1])
+
+
+def test_coarsest_eigenpairs_closed_forms(oracle_mod):
+    n = 30
+    p = W.path(n)
+    lam, U = oracle_mod.coarsest_eigenpairs(p.n, p.u, p.v, p.w, 6, False)
+    assert np.allclose(lam, 4 * np.sin(np.pi * np.arange(6) / (2 * n)) ** 2, atol=1e-12)
+    assert np.allclose(U.T @ U, np.eye(6), atol=1e-12)
+    # normalised cut on a regular graph: the spectrum divides by the degree
+    c = _cycle_weighted(20, 2.0)
+    lam_n, Un = oracle_mod.coarsest_eigenpairs(c.n, c.u, c.v, c.w, 5, True)
+    lam_r, _ = oracle_mod.coarsest_eigenpairs(c.n, c.u, c.v, c.w, 5, False)
+    assert np.allclose(lam_n, lam_r / 4.0, atol=1e-12)
+
+
+def test_coarsest_eigenpairs_generalized_against_lapack(oracle_mod):
+    from scipy.linalg import eigh
+    g = W.random_sparse(35, 120, seed=12)
+    L = oracle_mod.dense_laplacian(g.n, g.u, g.v, g.w)
+    D = np.diag(np.diag(L))
+    lam, U = oracle_mod.coarsest_eigenpairs(g.n, g.u, g.v, g.w, 8, True)
+    ref = eigh(L, D, eigvals_only=True)[:8]
+    assert np.allclose(lam, ref, atol=1e-11)
+    assert np.max(np.abs(L @ U - (D @ U) * lam)) <= 1e-10
+    assert np.allclose(U.T @ D @ U, np.eye(8), atol=1e-10)  # B-orthonormal
+
+
+def test_gram_schmidt_properties(oracle_mod):
+    rng = np.random.default_rng(13)
+    A = rng.normal(size=(50, 6))
+    Q = oracle_mod.gram_schmidt(A)
+    assert np.allclose(Q.T @ Q, np.eye(6), atol=1e-12)
+    # column order: span(Q[:, :j]) = span(A[:, :j]) for every j, and the
+    # first column is the first input column normalised
+    for j in range(1, 7):
+        P = Q[:, :j] @ Q[:, :j].T
+        assert np.allclose(P @ A[:, :j], A[:, :j], atol=1e-10)
+    assert np.allclose(Q[:, 0], A[:, 0] / np.linalg.norm(A[:, 0]))
+    # numpy's QR gives the same factor up to column signs
+    Qr, _ = np.linalg.qr(A)
+    assert np.allclose(np.abs(np.sum(Qr * Q, 0)), 1.0, atol=1e-10)
+
+
+def test_multilevel_eigensolve_single_level_is_exact(oracle_mod):
+    n = 40
+    p = W.path(n)
+    U, lam = oracle_mod.multilevel_eigensolve([(p.n, p.u, p.v, p.w)], [], 5)
+    L = oracle_mod.dense_laplacian(p.n, p.u, p.v, p.w)
+    rq = np.sum(U * (L @ U), 0)
+    assert np.allclose(rq, 4 * np.sin(np.pi * np.arange(5) / (2 * n)) ** 2, atol=1e-12)
+
+
+def test_multilevel_eigensolve_prolongation_and_refinement(oracle_mod):
+    # two levels of a path: pairs (2i, 2i+1) aggregated; with no smoothing the
+    # result is constant on every pair, and smoothing lowers the Rayleigh
+    # quotients of the low modes toward the true eigenvalues
+    n = 64
+    p = W.path(n)
+    agg = (np.arange(n) // 2).astype(np.int32)
+    uc, vc, wc = oracle_mod.coarsen(p.n, p.u, p.v, p.w, agg, n // 2)
+    graphs = [(p.n, p.u, p.v, p.w), (n // 2, uc, vc, wc)]
+    U0, lam = oracle_mod.multilevel_eigensolve(graphs, [agg], 4, iters=0)
+    assert np.allclose(U0[0::2], U0[1::2], atol=0)
+    assert np.allclose(U0.T @ U0, np.eye(4), atol=1e-12)
+    L = oracle_mod.dense_laplacian(p.n, p.u, p.v, p.w)
+    U1, _ = oracle_mod.multilevel_eigensolve(graphs, [agg], 4, iters=20)
+    exact = 4 * np.sin(np.pi * np.arange(4) / (2 * n)) ** 2
+    rq0 = np.sum(U0 * (L @ U0), 0)
+    rq1 = np.sum(U1 * (L @ U1), 0)
+    # the first column stays the constant vector (shift 0 fixes it), so every
+    # later column is orthogonal to it and, by Courant-Fischer, its Rayleigh
+    # quotient is at least the second eigenvalue
+    assert np.allclose(U1[:, 0], U1[0, 0], atol=1e-12)
+    assert np.all(rq0[1:] >= exact[1] - 1e-12) and np.all(rq1[1:] >= exact[1] - 1e-12)
+    assert np.all(np.abs(rq1[1:] - exact[1:]) < np.abs(rq0[1:] - exact[1:]))
