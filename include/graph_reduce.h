@@ -159,6 +159,29 @@ gr_status graph_reduce_get_edges(const gr_ctx* ctx, int64_t* m_out, int32_t* u, 
  * GR_ESTATE for a context not made by coarsen. */
 gr_status graph_reduce_get_map(const gr_ctx* ctx, int32_t* agg_out, int64_t* n_parent_out);
 
+/* Multilevel Laplacian eigensolver (Alg. 5, Sec. 4.1; Eqs. equ:lgl and
+ * equ:lgs).  The first k eigenpairs of L u = lambda B u on the coarsest level
+ * (B = I for ratio cut, B = D for normalised cut) come from a dense FP64
+ * symmetric eigensolver; then, level by level toward the finest, the block is
+ * mapped with H = P (U_fine[i] = U_coarse[map[i]]) and every column k is
+ * smoothed by `iters` weighted-Jacobi iterations on (L - lambda_k B) y = 0,
+ *   y <- (1 - omega) y + omega (D - lambda_k B)^-1 A y,
+ * lambda_k being the coarsest eigenvalue (a row whose shifted diagonal is not
+ * positive keeps its value: the paper is silent there); the finest block is
+ * orthonormalised by modified Gram-Schmidt in column order.
+ *   levels        nlevels >= 1 contexts: levels[0] the finest graph, levels[l]
+ *                 (l >= 1) coarsened from levels[l-1] (its parent map is H)
+ *   k             1..32, at most the coarsest size (which must be <= 16384)
+ *   normalized    0: B = I, 1: B = D (a degree-0 node takes B = 1 on the
+ *                 coarsest level)
+ *   omega, iters  Jacobi weight (0, 1] and iterations per finer level
+ *   U_out         device, n_0 x k row-major FP64, on levels[0]'s stream
+ *   lambda_out    host, k FP64: the coarsest eigenvalues, ascending
+ *   rayleigh_out  host, k FP64: x'Lx / x'Bx of the returned columns, or NULL
+ * GR_EINVAL for a bad hierarchy or sizes; GR_ECUDA if the dense solver fails. */
+gr_status graph_reduce_eigensolve(gr_ctx* const* levels, int nlevels, int k, int normalized, double omega,
+                                  int iters, double* U_out, double* lambda_out, double* rayleigh_out);
+
 /* Parameters of the level loop. */
 typedef struct gr_params {
     int K;                 /* test vectors per level                          */

@@ -10,6 +10,7 @@ import ctypes
 import os
 from dataclasses import dataclass
 
+import numpy as np
 import torch
 
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libgraphreduce.so")
@@ -23,7 +24,7 @@ EXPORTED = [
     "graph_reduce_create", "graph_reduce_get_info", "graph_reduce_smooth", "graph_reduce_smooth_noalloc",
     "graph_reduce_affinity",
     "graph_reduce_aggregate", "graph_reduce_coarsen", "graph_reduce_get_edges", "graph_reduce_get_map",
-    "graph_reduce_multilevel", "graph_reduce_compose_maps", "graph_reduce_loss_fwd",
+    "graph_reduce_multilevel", "graph_reduce_compose_maps", "graph_reduce_eigensolve", "graph_reduce_loss_fwd",
     "graph_reduce_loss_bwd", "graph_reduce_launch_count", "graph_reduce_last_error", "graph_reduce_destroy",
 ]
 
@@ -76,6 +77,7 @@ def load():
         "graph_reduce_multilevel": (I, [P, ctypes.POINTER(gr_params), PP, ctypes.POINTER(I),
                                         ctypes.POINTER(gr_level_stats)]),
         "graph_reduce_compose_maps": (I, [PP, I, P]),
+        "graph_reduce_eigensolve": (I, [PP, I, I, I, D, I, P, P, P]),
         "graph_reduce_loss_fwd": (I, [P, P, P, P, I, P, I, D, P, P]),
         "graph_reduce_loss_bwd": (I, [P, P, I, P, I, D, P, P]),
         "graph_reduce_launch_count": (ctypes.c_uint64, []),
@@ -274,6 +276,22 @@ def graph_reduce_multilevel(g: Graph, params: ReduceParams, want_stats=True):
                             t_affinity=s.t_affinity, t_aggregate=s.t_aggregate, t_coarsen=s.t_coarsen,
                             t_sweeps=s.t_sweeps))
     return levels, out
+
+
+def graph_reduce_eigensolve(levels, k, normalized=False, omega=0.7, iters=10, want_rayleigh=True):
+    """Multilevel Laplacian eigensolver (Alg. 5) over ``levels`` = [finest
+    Graph, its coarsening, ...].  Returns (U, lam, rayleigh): U an n_0 x k FP64
+    device tensor, lam the coarsest eigenvalues, rayleigh the Rayleigh
+    quotients of U's columns (numpy arrays)."""
+    arr = (ctypes.c_void_p * len(levels))(*[lv.handle.value for lv in levels])
+    U = torch.empty(levels[0].n, k, dtype=torch.float64, device=levels[0].device)
+    lam = np.zeros(k, np.float64)
+    rq = np.zeros(k, np.float64) if want_rayleigh else None
+    st = load().graph_reduce_eigensolve(arr, len(levels), int(k), 1 if normalized else 0, float(omega), int(iters),
+                                        _ptr(U), lam.ctypes.data_as(ctypes.c_void_p),
+                                        rq.ctypes.data_as(ctypes.c_void_p) if rq is not None else None)
+    _check(st, levels[0].handle)
+    return U, lam, rq
 
 
 def graph_reduce_compose_maps(levels):

@@ -1,0 +1,333 @@
+// Multilevel Laplacian eigensolver (Alg. 5, Sec. 4.1; Eqs. equ:lgl, equ:lgs).
+//
+// Coarsest level: the first k eigenpairs of L u = lambda B u (B = I ratio
+// cut, B = D normalised cut) from a dense symmetric eigensolver (cuSOLVER
+// syevd; the coarsest graph is small).  Then, level by level toward the
+// finest: U_fine = P U_coarse (the parent map), and `iters` weighted-Jacobi
+// iterations on (L - lambda_k B) y = 0 for every column k, the shift being the
+// coarsest eigenvalue.  Finally modified Gram-Schmidt over the columns.  Every
+// reduction is FP64 with a fixed summation order (per-block partials, then a
+// last-block finish), so results are reproducible.
+#include <cusolverDn.h>
+
+#include "gr_internal.cuh"
+
+namespace gr {
+
+namespace {
+
+constexpr int ET = 256;
+
+// dense column-major L (or D^-1/2 L D^-1/2) of a small graph, thread per row
+__global__ void k_dense_laplacian(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                  const int32_t* __restrict__ eid, const double* __restrict__ ew,
+                                  const double* __restrict__ deg, int normalized, double* __restrict__ A) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double bi = deg[i] > 0.0 ? deg[i] : 1.0;
+    const double si = normalized ? 1.0 / sqrt(bi) : 1.0;
+    A[i + i * n] = si * deg[i] * si;
+    for (int64_t j = rowptr[i]; j < rowptr[i + 1]; ++j) {
+        const int64_t q = col[j];
+        const double bq = deg[q] > 0.0 ? deg[q] : 1.0;
+        const double sq = normalized ? 1.0 / sqrt(bq) : 1.0;
+        A[i + q * n] = si * (-ew[eid[j]]) * sq;
+    }
+}
+
+// first k eigenvectors (columns of the column-major A) into a row-major n x k
+// block, mapped back by D^-1/2 for the normalised problem
+__global__ void k_take_eigvecs(int64_t n, int k, const double* __restrict__ A, const double* __restrict__ deg,
+                               int normalized, double* __restrict__ U) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * k) return;
+    const int64_t i = idx / k;
+    const int c = (int)(idx % k);
+    double x = A[i + (int64_t)c * n];
+    if (normalized) {
+        const double b = deg[i] > 0.0 ? deg[i] : 1.0;
+        x = x / sqrt(b);
+    }
+    U[idx] = x;
+}
+
+// U_fine[i, :] = U_coarse[map[i], :]  (H = P, Alg. 5 step 5)
+__global__ void k_prolong(int64_t n, int k, const int32_t* __restrict__ map, const double* __restrict__ Uc,
+                          double* __restrict__ Uf) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * k) return;
+    const int64_t i = idx / k;
+    const int c = (int)(idx % k);
+    Uf[idx] = Uc[(int64_t)map[i] * k + c];
+}
+
+// One weighted-Jacobi iteration on (L - lambda_c B) y = 0 for every column c,
+// thread per (row, column): y <- (1 - w) y + w (A y)_r / (D_r - lambda_c B_r),
+// with (A y)_r = D_r (D^-1 A y)_r from the row-scaled weights; a row whose
+// shifted diagonal is not positive keeps its value.
+__global__ void k_shifted_jacobi(int64_t n, int k, const int64_t* __restrict__ rowptr,
+                                 const int32_t* __restrict__ col, const double* __restrict__ wn64,
+                                 const double* __restrict__ deg, const double* __restrict__ lam, int normalized,
+                                 double omega, const double* __restrict__ Yin, double* __restrict__ Yout) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * k) return;
+    const int64_t r = idx / k;
+    const int c = (int)(idx % k);
+    const double y = Yin[idx];
+    const double D = deg[r];
+    const double diag = D - lam[c] * (normalized ? D : 1.0);
+    if (!(diag > 0.0)) {
+        Yout[idx] = y;
+        return;
+    }
+    double s = 0.0;
+    for (int64_t j = rowptr[r]; j < rowptr[r + 1]; ++j) s += wn64[j] * Yin[(int64_t)col[j] * k + c];
+    Yout[idx] = (1.0 - omega) * y + omega * (s * D / diag);
+}
+
+// row-major n x k <-> column-major
+__global__ void k_to_colmajor(int64_t n, int k, const double* __restrict__ U, double* __restrict__ V) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * k) return;
+    V[(idx % k) * n + idx / k] = U[idx];
+}
+__global__ void k_to_rowmajor(int64_t n, int k, const double* __restrict__ V, double* __restrict__ U) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * k) return;
+    U[idx] = V[(idx % k) * n + idx / k];
+}
+
+// Sum of one double per thread over the block, in a fixed order.
+__device__ __forceinline__ double block_sum(double s, double* red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < ET / 32; ++w) t += red[w];
+    __syncthreads();
+    return t;  // valid in thread 0
+}
+
+// Per-block partial of a grid reduction; the last block to arrive adds the
+// partials (thread t takes blocks t, t + ET, ... in order, then block_sum).
+__device__ __forceinline__ void grid_finish(double s, double* __restrict__ part, unsigned* __restrict__ counter,
+                                            double* __restrict__ out) {
+    __shared__ double red[ET / 32];
+    __shared__ bool last;
+    const double t = block_sum(s, red);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = t;
+        __threadfence();
+        last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last) {
+        __threadfence();
+        double a = 0.0;
+        for (unsigned b = threadIdx.x; b < gridDim.x; b += ET) a += __ldcg(part + b);
+        const double total = block_sum(a, red);
+        if (threadIdx.x == 0) {
+            *out = total;
+            *counter = 0u;
+        }
+    }
+}
+
+// out = a . b over n entries: per-block partials, the last block to finish
+// adds them in block order (one atomic ticket, no wait)
+__global__ void __launch_bounds__(ET) k_dot(int64_t n, const double* __restrict__ a, const double* __restrict__ b,
+                                            double* __restrict__ part, unsigned* __restrict__ counter,
+                                            double* __restrict__ out) {
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        s += a[i] * b[i];
+    grid_finish(s, part, counter, out);
+}
+
+// y -= r x  (r = *rp)
+__global__ void k_axpy(int64_t n, const double* __restrict__ rp, const double* __restrict__ x,
+                       double* __restrict__ y) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] -= (*rp) * x[i];
+}
+
+// y /= sqrt(*nrm2)
+__global__ void k_unit(int64_t n, const double* __restrict__ nrm2, double* __restrict__ y) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] /= sqrt(*nrm2);
+}
+
+// per-edge sum over the canonical list of w (x_u - x_v)^2 for column x (= x' L x),
+// with the same block-partial / last-block finish
+__global__ void __launch_bounds__(ET) k_edge_quad(int64_t m, const int32_t* __restrict__ eu,
+                                                  const int32_t* __restrict__ ev, const double* __restrict__ ew,
+                                                  const double* __restrict__ x, double* __restrict__ part,
+                                                  unsigned* __restrict__ counter, double* __restrict__ out) {
+    double s = 0.0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+        const double d = x[eu[e]] - x[ev[e]];
+        s += ew[e] * d * d;
+    }
+    grid_finish(s, part, counter, out);
+}
+
+// x' B x for B = D (x' x for B = I uses k_dot)
+__global__ void k_scale_by(int64_t n, const double* __restrict__ x, const double* __restrict__ deg,
+                           double* __restrict__ y) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = x[i] * deg[i];
+}
+
+}  // namespace
+
+gr_status eigensolve_impl(gr_ctx* const* levels, int nlevels, int k, int normalized, double omega, int iters,
+                          double* U_out, double* lambda_out, double* rayleigh_out) {
+    gr_ctx* f = levels[0];
+    gr_ctx* c = levels[nlevels - 1];
+    cudaStream_t s = f->stream;
+    const int64_t nc = c->n, n0 = f->n;
+    auto blocks = [](int64_t work) { return (unsigned)ceil_div(work > 0 ? work : 1, ET); };
+
+    // scratch: dense matrix, eigenvalues, two n x k blocks at the finest size,
+    // column-major copy, reduction partials, scalars
+    int64_t nmax = 0;
+    for (int l = 0; l < nlevels; ++l) nmax = levels[l]->n > nmax ? levels[l]->n : nmax;
+    const int RB = f->num_sms * 4;  // reduction blocks
+    size_t need = 0;
+    auto add = [&](size_t bytes) {
+        size_t off = need;
+        need += (bytes + 255) & ~size_t(255);
+        return off;
+    };
+    const size_t o_A = add(sizeof(double) * (size_t)nc * (size_t)nc), o_W = add(sizeof(double) * (size_t)nc),
+                 o_Y0 = add(sizeof(double) * (size_t)nmax * k), o_Y1 = add(sizeof(double) * (size_t)nmax * k),
+                 o_V = add(sizeof(double) * (size_t)n0 * k), o_T = add(sizeof(double) * (size_t)n0),
+                 o_part = add(sizeof(double) * (size_t)RB), o_sc = add(sizeof(double) * 64),
+                 o_lam = add(sizeof(double) * 32), o_ctr = add(64), o_info = add(64);
+    void* base;
+    GR_TRY_CUDA(f, f->ws.get(WS_EIG, need, &base), "eigensolver scratch");
+    char* Bp = (char*)base;
+    double* A = (double*)(Bp + o_A);
+    double* W = (double*)(Bp + o_W);
+    double* Y[2] = {(double*)(Bp + o_Y0), (double*)(Bp + o_Y1)};
+    double* V = (double*)(Bp + o_V);
+    double* T = (double*)(Bp + o_T);
+    double* part = (double*)(Bp + o_part);
+    double* sc = (double*)(Bp + o_sc);
+    double* lam = (double*)(Bp + o_lam);
+    unsigned* ctr = (unsigned*)(Bp + o_ctr);
+    int* info = (int*)(Bp + o_info);
+    GR_TRY_CUDA(f, cudaMemsetAsync(ctr, 0, 64, s), "memset");
+
+    // 1) coarsest eigenpairs (Alg. 5 step 2, Eq. equ:lgs)
+    GR_TRY_CUDA(f, cudaMemsetAsync(A, 0, sizeof(double) * (size_t)nc * (size_t)nc, s), "memset");
+    k_dense_laplacian<<<blocks(nc), ET, 0, s>>>(nc, c->rowptr, c->col, c->eid, c->ew, c->deg, normalized, A);
+    count_launch();
+    // one solver handle per host thread and device, kept for later calls
+    static thread_local cusolverDnHandle_t h = nullptr;
+    static thread_local int h_dev = -1;
+    if (h && h_dev != f->device) {
+        cusolverDnDestroy(h);
+        h = nullptr;
+    }
+    if (!h) {
+        if (cusolverDnCreate(&h) != CUSOLVER_STATUS_SUCCESS) {
+            h = nullptr;
+            return set_error(f, GR_ECUDA, "eigensolve: cusolver init");
+        }
+        h_dev = f->device;
+    }
+    if (cusolverDnSetStream(h, s) != CUSOLVER_STATUS_SUCCESS) return set_error(f, GR_ECUDA, "eigensolve: stream");
+    int lwork = 0;
+    if (cusolverDnDsyevd_bufferSize(h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, (int)nc, A, (int)nc, W,
+                                    &lwork) != CUSOLVER_STATUS_SUCCESS)
+        return set_error(f, GR_ECUDA, "eigensolve: workspace query");
+    void* pw;
+    GR_TRY_CUDA(f, f->ws.get(WS_EIG_WORK, sizeof(double) * (size_t)(lwork > 0 ? lwork : 1), &pw), "scratch");
+    if (cusolverDnDsyevd(h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, (int)nc, A, (int)nc, W, (double*)pw,
+                         lwork, info) != CUSOLVER_STATUS_SUCCESS)
+        return set_error(f, GR_ECUDA, "eigensolve: syevd");
+    int64_t* hs = host_scratch();
+    if (!hs) return set_error(f, GR_ENOMEM, "eigensolve: pinned scratch unavailable");
+    GR_TRY_CUDA(f, cudaMemcpyAsync(hs, info, sizeof(int), cudaMemcpyDeviceToHost, s), "readback");
+    GR_TRY_CUDA(f, cudaMemcpyAsync(lam, W, sizeof(double) * (size_t)k, cudaMemcpyDeviceToDevice, s), "copy");
+    GR_TRY_CUDA(f, cudaMemcpyAsync(lambda_out, W, sizeof(double) * (size_t)k, cudaMemcpyDeviceToHost, s), "copy");
+    GR_TRY_CUDA(f, cudaStreamSynchronize(s), "sync");
+    if (((int*)hs)[0] != 0) return set_error(f, GR_ECUDA, "eigensolve: the dense eigensolver did not converge");
+    int cur = 0;
+    k_take_eigvecs<<<blocks(nc * k), ET, 0, s>>>(nc, k, A, c->deg, normalized, Y[cur]);
+    count_launch();
+
+    // 2) map and smooth, level by level (Alg. 5 steps 4-10)
+    for (int l = nlevels - 2; l >= 0; --l) {
+        gr_ctx* g = levels[l];
+        const int64_t n = g->n;
+        k_prolong<<<blocks(n * k), ET, 0, s>>>(n, k, levels[l + 1]->parent_map, Y[cur], Y[cur ^ 1]);
+        count_launch();
+        cur ^= 1;
+        for (int it = 0; it < iters; ++it) {
+            k_shifted_jacobi<<<blocks(n * k), ET, 0, s>>>(n, k, g->rowptr, g->col, g->wn64, g->deg, lam, normalized,
+                                                        omega, Y[cur], Y[cur ^ 1]);
+            count_launch();
+            cur ^= 1;
+        }
+    }
+
+    // 3) modified Gram-Schmidt over the columns (Alg. 5 step 11)
+    k_to_colmajor<<<blocks(n0 * k), ET, 0, s>>>(n0, k, Y[cur], V);
+    count_launch();
+    const unsigned rb = (unsigned)(RB < ceil_div(n0, ET) ? RB : ceil_div(n0 > 0 ? n0 : 1, ET));
+    for (int i = 0; i < k; ++i) {
+        double* ui = V + (int64_t)i * n0;
+        for (int j = 0; j < i; ++j) {
+            const double* uj = V + (int64_t)j * n0;
+            k_dot<<<rb, ET, 0, s>>>(n0, uj, ui, part, ctr, sc);
+            count_launch();
+            k_axpy<<<blocks(n0), ET, 0, s>>>(n0, sc, uj, ui);
+            count_launch();
+        }
+        k_dot<<<rb, ET, 0, s>>>(n0, ui, ui, part, ctr, sc);
+        count_launch();
+        k_unit<<<blocks(n0), ET, 0, s>>>(n0, sc, ui);
+        count_launch();
+    }
+    k_to_rowmajor<<<blocks(n0 * k), ET, 0, s>>>(n0, k, V, U_out);
+    count_launch();
+
+    // 4) Rayleigh quotients of the result, x' L x / x' B x
+    if (rayleigh_out) {
+        const unsigned rbm = (unsigned)(RB < ceil_div(f->m, ET) ? RB : ceil_div(f->m > 0 ? f->m : 1, ET));
+        for (int i = 0; i < k; ++i) {
+            const double* ui = V + (int64_t)i * n0;
+            if (f->m > 0) {
+                k_edge_quad<<<rbm, ET, 0, s>>>(f->m, f->eu, f->ev, f->ew, ui, part, ctr, sc + 2 * i);
+                count_launch();
+            } else {
+                GR_TRY_CUDA(f, cudaMemsetAsync(sc + 2 * i, 0, sizeof(double), s), "memset");
+            }
+            const double* bu = ui;
+            if (normalized) {
+                k_scale_by<<<blocks(n0), ET, 0, s>>>(n0, ui, f->deg, T);
+                count_launch();
+                bu = T;
+            }
+            k_dot<<<rb, ET, 0, s>>>(n0, ui, bu, part, ctr, sc + 2 * i + 1);
+            count_launch();
+        }
+        double* hq = (double*)hs;  // 64 B: up to 4 pairs at a time
+        for (int i0 = 0; i0 < k; i0 += 4) {
+            const int cnt = k - i0 < 4 ? k - i0 : 4;
+            GR_TRY_CUDA(f, cudaMemcpyAsync(hq, sc + 2 * i0, sizeof(double) * 2 * cnt, cudaMemcpyDeviceToHost, s),
+                        "readback");
+            GR_TRY_CUDA(f, cudaStreamSynchronize(s), "sync");
+            for (int t = 0; t < cnt; ++t) rayleigh_out[i0 + t] = hq[2 * t] / hq[2 * t + 1];
+        }
+    }
+    GR_TRY_CUDA(f, cudaGetLastError(), "eigensolve kernels");
+    GR_TRY_CUDA(f, cudaStreamSynchronize(s), "sync");
+    return GR_OK;
+}
+
+}  // namespace gr

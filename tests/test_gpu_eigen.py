@@ -1,0 +1,100 @@
+"""Multilevel Laplacian eigensolver (Alg. 5) on the GPU against the oracle.
+
+The hierarchy comes from the oracle's own reduction; the GPU contexts are
+rebuilt from the oracle's aggregate maps with graph_reduce_coarsen, so both
+sides solve the same problem and no oracle input comes from the CUDA path.
+Eigenvectors are compared up to the sign of each column (a dense eigensolver
+fixes none); the graphs have random weights, so the eigenvalues are simple.
+"""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def gr():
+    from paper_1812_08942_gb300 import build as B
+    B.build()
+    import paper_1812_08942_gb300 as gr
+    gr.load()
+    return gr
+
+
+def _hierarchy(gr, oracle_mod, g, final, K=8, sweeps=5):
+    levels = oracle_mod.reduce_multilevel(g.n, g.u, g.v, g.w, K, sweeps, final_target=final)
+    graphs = [(g.n, g.u, g.v, g.w)] + [(lv.nc, lv.uc, lv.vc, lv.wc) for lv in levels]
+    maps = [lv.agg for lv in levels]
+    G = gr.graph_reduce_create(g.n, g.u, g.v, g.w)
+    ctxs = [G]
+    for lv in levels:
+        ctxs.append(gr.graph_reduce_coarsen(ctxs[-1], torch.from_numpy(lv.agg).to(DEV), lv.nc))
+    return graphs, maps, ctxs
+
+
+def _compare(U, Ur, tol):
+    U = U.cpu().numpy()
+    s = np.sign(np.sum(U * Ur, 0))
+    s[s == 0] = 1.0
+    return np.max(np.abs(U * s - Ur)) <= tol
+
+
+CASES = [
+    ("mesh_ratio", lambda: W.mesh3d(14, 12, 10, seed=21), 300, False, 6, 8),
+    ("mesh_normalized", lambda: W.mesh3d(14, 12, 10, seed=22), 300, True, 6, 8),
+    ("rand_ratio_k13", lambda: W.random_sparse(3001, 12000, seed=23), 500, False, 13, 5),
+    ("rand_normalized_k1", lambda: W.random_sparse(2500, 9000, seed=24), 400, True, 1, 5),
+    ("knn_ratio", lambda: W.knn_gmm(4000, 8, 1, 6, 25), 250, False, 8, 10),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_eigensolve_parity(gr, oracle_mod, case):
+    _, make, final, normalized, k, iters = case
+    g = make()
+    assert oracle_mod.n_components(g.n, g.u, g.v) == 1  # else lambda = 0 repeats and bases differ
+    graphs, maps, ctxs = _hierarchy(gr, oracle_mod, g, final)
+    assert len(ctxs) >= 3
+    Ur, lam_r = oracle_mod.multilevel_eigensolve(graphs, maps, k, normalized, 0.7, iters)
+    U, lam, rq = gr.graph_reduce_eigensolve(ctxs, k, normalized, 0.7, iters)
+    assert np.allclose(lam, lam_r, rtol=1e-10, atol=1e-12)
+    assert _compare(U, Ur, 1e-8)
+    L = oracle_mod.sparse_laplacian(g.n, g.u, g.v, g.w)
+    B = L.diagonal() if normalized else np.ones(g.n)
+    rq_r = np.sum(Ur * (L @ Ur), 0) / np.sum(Ur * Ur * B[:, None], 0)
+    assert np.allclose(rq, rq_r, rtol=1e-9, atol=1e-12)
+
+
+def test_eigensolve_single_level_and_no_smoothing(gr, oracle_mod):
+    g = W.random_sparse(600, 2500, seed=26)
+    G = gr.graph_reduce_create(g.n, g.u, g.v, g.w)
+    U, lam, rq = gr.graph_reduce_eigensolve([G], 5, False, 0.7, 10)
+    ref = np.sort(np.linalg.eigvalsh(oracle_mod.dense_laplacian(g.n, g.u, g.v, g.w)))[:5]
+    assert np.allclose(lam, ref, atol=1e-10) and np.allclose(rq, ref, atol=1e-10)
+    Uh = U.cpu().numpy()
+    assert np.allclose(Uh.T @ Uh, np.eye(5), atol=1e-12)
+    # iters = 0: the finest block is the mapped coarse block, orthonormalised
+    graphs, maps, ctxs = _hierarchy(gr, oracle_mod, g, 100)
+    Ur, _ = oracle_mod.multilevel_eigensolve(graphs, maps, 4, False, 0.7, 0)
+    U0, _, _ = gr.graph_reduce_eigensolve(ctxs, 4, False, 0.7, 0)
+    assert _compare(U0, Ur, 1e-9)
+
+
+def test_eigensolve_rejects_bad_requests(gr, oracle_mod):
+    g = W.random_sparse(500, 2000, seed=27)
+    graphs, maps, ctxs = _hierarchy(gr, oracle_mod, g, 100)
+    with pytest.raises(gr.GraphReduceError) as ei:
+        gr.graph_reduce_eigensolve(ctxs, ctxs[-1].n + 1)
+    assert ei.value.status == 1
+    with pytest.raises(gr.GraphReduceError):
+        gr.graph_reduce_eigensolve(ctxs, 33)
+    with pytest.raises(gr.GraphReduceError):  # levels out of order
+        gr.graph_reduce_eigensolve([ctxs[0], ctxs[2]], 4)
+    big = W.mesh3d(30, 30, 20, seed=28)  # 18,000 nodes on the coarsest (only) level
+    B = gr.graph_reduce_create(big.n, big.u, big.v, big.w)
+    with pytest.raises(gr.GraphReduceError):
+        gr.graph_reduce_eigensolve([B], 4)
