@@ -318,6 +318,24 @@ def multilevel_eigensolve(graphs, maps, k, normalized=False, omega=0.7, iters=10
 
 
 # --------------------------------------------------------------------------
+# Reduced data set (Alg. 6, step 4): F_R = H_G^R F with H_G^R = P^T
+# --------------------------------------------------------------------------
+def reduce_features(agg, nc, F, mean=False):
+    """F_R[A] = sum of F[i] over the fine nodes i with agg[i] = A, added in
+    ascending i in FP64 (np.add.at applies the updates in index order);
+    mean=True divides by the member count (empty aggregates stay 0)."""
+    F = np.asarray(F, dtype=np.float64)
+    agg = np.asarray(agg, np.int64)
+    out = np.zeros((nc,) + F.shape[1:], np.float64)
+    np.add.at(out, agg, F)
+    if mean:
+        cnt = np.bincount(agg, minlength=nc).astype(np.float64)
+        nz = cnt > 0
+        out[nz] = out[nz] / cnt[nz].reshape((-1,) + (1,) * (F.ndim - 1))
+    return out
+
+
+# --------------------------------------------------------------------------
 # Eigenvalue check (method of the paper's eigenvalue figure for fe_tooth):
 # the smallest nontrivial Laplacian eigenvalues, FP64 on the CPU.
 # --------------------------------------------------------------------------

@@ -668,3 +668,31 @@ def test_multilevel_eigensolve_prolongation_and_refinement(oracle_mod):
     assert np.allclose(U1[:, 0], U1[0, 0], atol=1e-12)
     assert np.all(rq0[1:] >= exact[1] - 1e-12) and np.all(rq1[1:] >= exact[1] - 1e-12)
     assert np.all(np.abs(rq1[1:] - exact[1:]) < np.abs(rq0[1:] - exact[1:]))
+
+
+# ---------------------------------------------------------------------------
+# Reduced data set (Alg. 6, step 4): F_R = P^T F
+# ---------------------------------------------------------------------------
+def test_reduce_features_against_dense_product(oracle_mod):
+    rng = np.random.default_rng(31)
+    n, nc, d = 200, 37, 5
+    agg = np.concatenate([np.arange(nc), rng.integers(0, nc, n - nc)]).astype(np.int32)
+    F = rng.normal(size=(n, d))
+    P = np.zeros((n, nc))
+    P[np.arange(n), agg] = 1.0
+    assert np.allclose(oracle_mod.reduce_features(agg, nc, F), P.T @ F, atol=1e-12)
+    # mean: (P^T P)^-1 P^T F
+    M = np.diag(1.0 / np.diag(P.T @ P))
+    assert np.allclose(oracle_mod.reduce_features(agg, nc, F, mean=True), M @ P.T @ F, atol=1e-12)
+
+
+def test_reduce_features_invariants(oracle_mod):
+    rng = np.random.default_rng(32)
+    n, nc = 300, 40
+    agg = np.concatenate([np.arange(nc), rng.integers(0, nc, n - nc)]).astype(np.int32)
+    Fi = rng.integers(-50, 50, size=(n, 3)).astype(np.float64)  # integers: every sum exact
+    R = oracle_mod.reduce_features(agg, nc, Fi)
+    assert np.array_equal(R.sum(0), Fi.sum(0))
+    assert np.array_equal(oracle_mod.reduce_features(np.arange(n, dtype=np.int32), n, Fi), Fi)
+    c = np.full((n, 2), 2.5)
+    assert np.array_equal(oracle_mod.reduce_features(agg, nc, c, mean=True), np.full((nc, 2), 2.5))
