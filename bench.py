@@ -406,7 +406,8 @@ def main():
         del G32, lv32, G64, lv64
 
     # Multilevel Laplacian eigensolver (Alg. 5) on a deeper reduction of the
-    # same graph: k = 8 ratio-cut eigenvectors, 10 shifted Jacobi iterations
+    # same graph (down to 1,024 nodes, where the dense FP64 eigensolve runs):
+    # k = 8 ratio-cut eigenvectors, 10 shifted Jacobi iterations
     # per level.  The smoothing time is the difference against 0 iterations;
     # its roofline counts, per iteration on each level, the CSR slots
     # (column + FP64 weight), row pointers and degrees, and the block read and
@@ -415,7 +416,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_eigen:
         keig, iters = 8, 10
         pe = gr.ReduceParams(K=wl.K, sweeps=wl.sweeps, omega=wl.omega, seed=0, prec=prec, passes=2,
-                             level_ratio=4, final_target=2048, max_levels=32)
+                             level_ratio=4, final_target=1024, max_levels=32)
         Ge = gr.graph_reduce_create(g.n, u_d, v_d, w_d)
         lve, _ = gr.graph_reduce_multilevel(Ge, pe, want_stats=False)
         hier = [Ge] + list(lve)
@@ -447,6 +448,30 @@ def main():
                "lambda_coarsest": [float(x) for x in lam], "rayleigh": [float(x) for x in rq]}
         del U, hier, lve, Ge
 
+    # Reduced data set F_R = P^T F (Alg. 6, step 4) over the bench step's
+    # levels: 16 FP32 features per fine node.  Algorithmic bytes: F read
+    # once, F_R written once, the per-level maps read once.
+    rdata = None
+    if rank == 0 and world == 1 and not args.no_eigen:
+        Gd = gr.graph_reduce_create(g.n, u_d, v_d, w_d)
+        lvd, _ = gr.graph_reduce_multilevel(Gd, params, want_stats=False)
+        Fd = torch.randn(g.n, 16, dtype=torch.float32, device=dev)
+        gr.graph_reduce_reduce_data(lvd, Fd)
+        tds = []
+        for _ in range(5):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            Rd = gr.graph_reduce_reduce_data(lvd, Fd)
+            e1.record()
+            torch.cuda.synchronize()
+            tds.append(e0.elapsed_time(e1))
+        tdm = min(tds)
+        dbytes = g.n * 16 * 4 + lvd[-1].n * 16 * 4 + 4 * (g.n + sum(L.n for L in lvd[:-1]))
+        rdata = {"d": 16, "dtype": "f32", "rows_in": g.n, "rows_out": lvd[-1].n, "ms": tdm,
+                 "algorithmic_bytes": dbytes, "achieved_gbs": dbytes / (tdm / 1000.0) / 1e9}
+        del Rd, Fd, lvd, Gd
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         gs, desc = oracle_sample_graph(args.workload)
@@ -466,7 +491,7 @@ def main():
                        "l2": "inputs larger than L2 (edge list %.0f MB + CSR %.0f MB vs 129 MB); no flush"
                              % (g.m * 16 / 1e6, g.m * 2 * 24 / 1e6)},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-            "fp32_vs_fp64": cmp64, "multilevel_eigensolver": eig,
+            "fp32_vs_fp64": cmp64, "multilevel_eigensolver": eig, "reduced_dataset": rdata,
             "clocks": clocks, "levels": per_level,
         }
         print(json.dumps(line), flush=True)

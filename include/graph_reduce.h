@@ -159,6 +159,19 @@ gr_status graph_reduce_get_edges(const gr_ctx* ctx, int64_t* m_out, int32_t* u, 
  * GR_ESTATE for a context not made by coarsen. */
 gr_status graph_reduce_get_map(const gr_ctx* ctx, int32_t* agg_out, int64_t* n_parent_out);
 
+/* Reduced data set F_R = H_G^R F (Alg. 6, step 4) with H_G^R = P^T composed
+ * over the levels: row A of F_R is the sum of the rows of the fine nodes that
+ * end in coarsest aggregate A, added in ascending fine id in FP64 (mean = 1
+ * divides by the member count instead -- the paper names no normalisation;
+ * the plain P^T sum is its operator).
+ *   levels   nlevels >= 1 coarse contexts as from graph_reduce_multilevel
+ *            (levels[0] coarsened from the fine graph, each the next one's parent)
+ *   F        device, n_fine x d row-major, double if f64 else float
+ *   F_out    device, n_coarsest x d, same type
+ * GR_ESTATE if a level does not come from coarsen; GR_EINVAL for bad sizes. */
+gr_status graph_reduce_reduce_data(gr_ctx* const* levels, int nlevels, const void* F, int d, int f64, int mean,
+                                   void* F_out);
+
 /* Multilevel Laplacian eigensolver (Alg. 5, Sec. 4.1; Eqs. equ:lgl and
  * equ:lgs).  The first k eigenpairs of L u = lambda B u on the coarsest level
  * (B = I for ratio cut, B = D for normalised cut) come from a dense FP64

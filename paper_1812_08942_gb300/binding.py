@@ -24,7 +24,7 @@ EXPORTED = [
     "graph_reduce_create", "graph_reduce_get_info", "graph_reduce_smooth", "graph_reduce_smooth_noalloc",
     "graph_reduce_affinity",
     "graph_reduce_aggregate", "graph_reduce_coarsen", "graph_reduce_get_edges", "graph_reduce_get_map",
-    "graph_reduce_multilevel", "graph_reduce_compose_maps", "graph_reduce_eigensolve", "graph_reduce_loss_fwd",
+    "graph_reduce_multilevel", "graph_reduce_compose_maps", "graph_reduce_eigensolve", "graph_reduce_reduce_data", "graph_reduce_loss_fwd",
     "graph_reduce_loss_bwd", "graph_reduce_launch_count", "graph_reduce_last_error", "graph_reduce_destroy",
 ]
 
@@ -78,6 +78,7 @@ def load():
                                         ctypes.POINTER(gr_level_stats)]),
         "graph_reduce_compose_maps": (I, [PP, I, P]),
         "graph_reduce_eigensolve": (I, [PP, I, I, I, D, I, P, P, P]),
+        "graph_reduce_reduce_data": (I, [PP, I, P, I, I, I, P]),
         "graph_reduce_loss_fwd": (I, [P, P, P, P, I, P, I, D, P, P]),
         "graph_reduce_loss_bwd": (I, [P, P, I, P, I, D, P, P]),
         "graph_reduce_launch_count": (ctypes.c_uint64, []),
@@ -292,6 +293,19 @@ def graph_reduce_eigensolve(levels, k, normalized=False, omega=0.7, iters=10, wa
                                         rq.ctypes.data_as(ctypes.c_void_p) if rq is not None else None)
     _check(st, levels[0].handle)
     return U, lam, rq
+
+
+def graph_reduce_reduce_data(levels, F, mean=False):
+    """Reduced data set F_R = P^T F over coarse ``levels`` (as returned by
+    graph_reduce_multilevel); F is an n_fine x d float32/float64 CUDA tensor."""
+    assert F.is_cuda and F.dim() == 2 and F.dtype in (torch.float32, torch.float64)
+    F = F.contiguous()
+    arr = (ctypes.c_void_p * len(levels))(*[lv.handle.value for lv in levels])
+    out = torch.empty(levels[-1].n, F.shape[1], dtype=F.dtype, device=F.device)
+    st = load().graph_reduce_reduce_data(arr, len(levels), _ptr(F), int(F.shape[1]),
+                                         1 if F.dtype == torch.float64 else 0, 1 if mean else 0, _ptr(out))
+    _check(st, levels[0].handle)
+    return out
 
 
 def graph_reduce_compose_maps(levels):

@@ -183,6 +183,22 @@ gr_status graph_reduce_compose_maps(gr_ctx* const* levels, int nlevels, int32_t*
     return compose_impl(levels, nlevels, agg_out);
 }
 
+gr_status graph_reduce_reduce_data(gr_ctx* const* levels, int nlevels, const void* F, int d, int f64, int mean,
+                                   void* F_out) {
+    if (!levels || nlevels < 1 || !levels[0]) return set_error(nullptr, GR_EINVAL, "reduce_data: no levels");
+    gr_ctx* c0 = levels[0];
+    if (d < 0 || (f64 != 0 && f64 != 1) || (mean != 0 && mean != 1))
+        return set_error(c0, GR_EINVAL, "reduce_data: need d >= 0, f64 and mean in {0, 1}");
+    if (d > 0 && (!F || !F_out)) return set_error(c0, GR_EINVAL, "reduce_data: NULL data");
+    for (int l = 0; l < nlevels; ++l) {
+        if (!levels[l] || !levels[l]->parent_map)
+            return set_error(c0, GR_ESTATE, "reduce_data: every level must come from coarsen");
+        if (l > 0 && levels[l]->parent_n != levels[l - 1]->n)
+            return set_error(c0, GR_EINVAL, "reduce_data: levels do not chain");
+    }
+    return reduce_data_impl(levels, nlevels, F, d, f64, mean, F_out);
+}
+
 gr_status graph_reduce_eigensolve(gr_ctx* const* levels, int nlevels, int k, int normalized, double omega,
                                   int iters, double* U_out, double* lambda_out, double* rayleigh_out) {
     if (!levels || nlevels < 1 || !levels[0]) return set_error(nullptr, GR_EINVAL, "eigensolve: no levels");

@@ -2,7 +2,7 @@
 //
 // Coarsest level: the first k eigenpairs of L u = lambda B u (B = I ratio
 // cut, B = D normalised cut) from a dense symmetric eigensolver (cuSOLVER
-// syevd; the coarsest graph is small).  Then, level by level toward the
+// syevdx for the k smallest; the coarsest graph is small).  Then, level by level toward the
 // finest: U_fine = P U_coarse (the parent map), and `iters` weighted-Jacobi
 // iterations on (L - lambda_k B) y = 0 for every column k, the shift being the
 // coarsest eigenvalue.  Finally modified Gram-Schmidt over the columns.  Every
@@ -83,6 +83,62 @@ __global__ void k_shifted_jacobi(int64_t n, int k, const int64_t* __restrict__ r
     double s = 0.0;
     for (int64_t j = rowptr[r]; j < rowptr[r + 1]; ++j) s += wn64[j] * Yin[(int64_t)col[j] * k + c];
     Yout[idx] = (1.0 - omega) * y + omega * (s * D / diag);
+}
+
+// The same iteration with G lanes per row, each holding one 16-byte chunk
+// (two columns) of the row: the slot entries are read once per lane group and
+// each neighbour row is gathered chunk-wise; rows in grid-stride order.
+template <int K>
+__global__ void __launch_bounds__(ET) k_shifted_jacobi_rows(int64_t n64, const int64_t* __restrict__ rowptr,
+                                                           const int32_t* __restrict__ col,
+                                                           const double* __restrict__ wn64,
+                                                           const double* __restrict__ deg,
+                                                           const double* __restrict__ lam_in, int normalized,
+                                                           double omega, const double* __restrict__ Yin,
+                                                           double* __restrict__ Yout) {
+    constexpr int E = K >= 2 ? 2 : 1, G = K / E, RPW = 32 / G;
+    __shared__ double lam[K];
+    if (threadIdx.x < K) lam[threadIdx.x] = lam_in[threadIdx.x];
+    __syncthreads();
+    const int64_t n = n64;
+    const int lane = threadIdx.x & 31, seg = lane / G, q = lane % G;
+    if (seg >= RPW) return;
+    const int64_t stride = (((int64_t)gridDim.x * blockDim.x) >> 5) * RPW;
+    for (int64_t r = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * RPW + seg; r < n; r += stride) {
+        double acc[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) acc[e] = 0.0;
+        const int64_t j1 = rowptr[r + 1];
+        // two neighbour chunks in flight per step
+        for (int64_t j = rowptr[r]; j < j1; j += 2) {
+            const bool two = j + 1 < j1;
+            const double w0 = wn64[j], w1 = two ? wn64[j + 1] : 0.0;
+            const double* s0 = Yin + (int64_t)col[j] * K + q * E;
+            const double* s1 = Yin + (int64_t)col[two ? j + 1 : j] * K + q * E;
+            if constexpr (E == 2) {
+                const double2 x0 = __ldg(reinterpret_cast<const double2*>(s0));
+                const double2 x1 = __ldg(reinterpret_cast<const double2*>(s1));
+                acc[0] = fma(w0, x0.x, acc[0]);
+                acc[1] = fma(w0, x0.y, acc[1]);
+                if (two) {
+                    acc[0] = fma(w1, x1.x, acc[0]);
+                    acc[1] = fma(w1, x1.y, acc[1]);
+                }
+            } else {
+                const double x0 = __ldg(s0), x1 = __ldg(s1);
+                acc[0] = fma(w0, x0, acc[0]);
+                if (two) acc[0] = fma(w1, x1, acc[0]);
+            }
+        }
+        const double D = deg[r];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int c = q * E + e;
+            const double y = Yin[r * K + c];
+            const double diag = D - lam[c] * (normalized ? D : 1.0);
+            Yout[r * K + c] = diag > 0.0 ? (1.0 - omega) * y + omega * (acc[e] * D / diag) : y;
+        }
+    }
 }
 
 // row-major n x k <-> column-major
@@ -240,22 +296,24 @@ gr_status eigensolve_impl(gr_ctx* const* levels, int nlevels, int k, int normali
         h_dev = f->device;
     }
     if (cusolverDnSetStream(h, s) != CUSOLVER_STATUS_SUCCESS) return set_error(f, GR_ECUDA, "eigensolve: stream");
-    int lwork = 0;
-    if (cusolverDnDsyevd_bufferSize(h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, (int)nc, A, (int)nc, W,
-                                    &lwork) != CUSOLVER_STATUS_SUCCESS)
+    // only the k smallest eigenpairs (index range 1..k)
+    int lwork = 0, meig = 0;
+    if (cusolverDnDsyevdx_bufferSize(h, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_I, CUBLAS_FILL_MODE_LOWER,
+                                     (int)nc, A, (int)nc, 0.0, 0.0, 1, k, &meig, W, &lwork) != CUSOLVER_STATUS_SUCCESS)
         return set_error(f, GR_ECUDA, "eigensolve: workspace query");
     void* pw;
     GR_TRY_CUDA(f, f->ws.get(WS_EIG_WORK, sizeof(double) * (size_t)(lwork > 0 ? lwork : 1), &pw), "scratch");
-    if (cusolverDnDsyevd(h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, (int)nc, A, (int)nc, W, (double*)pw,
-                         lwork, info) != CUSOLVER_STATUS_SUCCESS)
-        return set_error(f, GR_ECUDA, "eigensolve: syevd");
+    if (cusolverDnDsyevdx(h, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_I, CUBLAS_FILL_MODE_LOWER, (int)nc, A,
+                          (int)nc, 0.0, 0.0, 1, k, &meig, W, (double*)pw, lwork, info) != CUSOLVER_STATUS_SUCCESS)
+        return set_error(f, GR_ECUDA, "eigensolve: syevdx");
     int64_t* hs = host_scratch();
     if (!hs) return set_error(f, GR_ENOMEM, "eigensolve: pinned scratch unavailable");
     GR_TRY_CUDA(f, cudaMemcpyAsync(hs, info, sizeof(int), cudaMemcpyDeviceToHost, s), "readback");
     GR_TRY_CUDA(f, cudaMemcpyAsync(lam, W, sizeof(double) * (size_t)k, cudaMemcpyDeviceToDevice, s), "copy");
     GR_TRY_CUDA(f, cudaMemcpyAsync(lambda_out, W, sizeof(double) * (size_t)k, cudaMemcpyDeviceToHost, s), "copy");
     GR_TRY_CUDA(f, cudaStreamSynchronize(s), "sync");
-    if (((int*)hs)[0] != 0) return set_error(f, GR_ECUDA, "eigensolve: the dense eigensolver did not converge");
+    if (((int*)hs)[0] != 0 || meig < k)
+        return set_error(f, GR_ECUDA, "eigensolve: the dense eigensolver did not converge");
     int cur = 0;
     k_take_eigvecs<<<blocks(nc * k), ET, 0, s>>>(nc, k, A, c->deg, normalized, Y[cur]);
     count_launch();
@@ -268,8 +326,21 @@ gr_status eigensolve_impl(gr_ctx* const* levels, int nlevels, int k, int normali
         count_launch();
         cur ^= 1;
         for (int it = 0; it < iters; ++it) {
-            k_shifted_jacobi<<<blocks(n * k), ET, 0, s>>>(n, k, g->rowptr, g->col, g->wn64, g->deg, lam, normalized,
-                                                        omega, Y[cur], Y[cur ^ 1]);
+            const unsigned gr = (unsigned)(f->num_sms * 8);
+#define GR_SJ_ROWS(KK)                                                                                         \
+    k_shifted_jacobi_rows<KK><<<gr, ET, 0, s>>>(n, g->rowptr, g->col, g->wn64, g->deg, lam, normalized, omega, \
+                                                Y[cur], Y[cur ^ 1])
+            switch (k) {
+                case 2: GR_SJ_ROWS(2); break;
+                case 4: GR_SJ_ROWS(4); break;
+                case 8: GR_SJ_ROWS(8); break;
+                case 16: GR_SJ_ROWS(16); break;
+                case 32: GR_SJ_ROWS(32); break;
+                default:
+                    k_shifted_jacobi<<<blocks(n * k), ET, 0, s>>>(n, k, g->rowptr, g->col, g->wn64, g->deg, lam,
+                                                                normalized, omega, Y[cur], Y[cur ^ 1]);
+            }
+#undef GR_SJ_ROWS
             count_launch();
             cur ^= 1;
         }

@@ -43,7 +43,7 @@ enum WsSlot {
     WS_AGG_STATE, WS_AGG_LIST, WS_AGG_KEYS, WS_AGG_SMALL,
     WS_COARSE_KEYS, WS_COARSE_VALS, WS_COARSE_TMP,
     WS_GAL_KEYS, WS_GAL_UCOL, WS_GAL_UW, WS_GAL_ROWS,
-    WS_EIG, WS_EIG_WORK,
+    WS_EIG, WS_EIG_WORK, WS_DATASET,
     WS_LOSS_A, WS_LOSS_B, WS_LOSS_C,
     WS_ML_X, WS_ML_D, WS_ML_AGG,
     WS_PINNED_UNUSED,
@@ -140,6 +140,9 @@ gr_status affinity_impl(gr_ctx* c, const void* X, int K, gr_prec prec, void* d, 
 gr_status aggregate_impl(gr_ctx* c, const void* d, int d_is_f64, int64_t target_nc, int passes,
                          int64_t max_proposals, int32_t* agg, int64_t* nc_out, int64_t* proposals_out);
 gr_status coarsen_impl(gr_ctx* c, const int32_t* agg, int64_t nc, gr_ctx** out);
+gr_status compose_impl(gr_ctx* const* levels, int nlevels, int32_t* out);
+gr_status reduce_data_impl(gr_ctx* const* levels, int nlevels, const void* F, int d, int f64, int mean,
+                           void* F_out);
 gr_status eigensolve_impl(gr_ctx* const* levels, int nlevels, int k, int normalized, double omega, int iters,
                           double* U_out, double* lambda_out, double* rayleigh_out);
 gr_status loss_fwd_impl(gr_ctx* fine, gr_ctx* coarse, const int32_t* agg, const float* X, int K,

@@ -4,7 +4,9 @@ The hierarchy comes from the oracle's own reduction; the GPU contexts are
 rebuilt from the oracle's aggregate maps with graph_reduce_coarsen, so both
 sides solve the same problem and no oracle input comes from the CUDA path.
 Eigenvectors are compared up to the sign of each column (a dense eigensolver
-fixes none); the graphs have random weights, so the eigenvalues are simple.
+fixes none); the graphs are connected and have random weights, so the
+eigenvalues are simple.  k = 2, 4, 8, 16, 32 take the row-chunk smoothing
+kernel, other k the thread-per-entry one.
 """
 import numpy as np
 import pytest
@@ -45,7 +47,9 @@ def _compare(U, Ur, tol):
 
 CASES = [
     ("mesh_ratio", lambda: W.mesh3d(14, 12, 10, seed=21), 300, False, 6, 8),
-    ("mesh_normalized", lambda: W.mesh3d(14, 12, 10, seed=22), 300, True, 6, 8),
+    ("mesh_normalized_k8", lambda: W.mesh3d(14, 12, 10, seed=22), 300, True, 8, 8),
+    ("rand_ratio_k16", lambda: W.random_sparse(3001, 12000, seed=29), 500, False, 16, 5),
+    ("rand_normalized_k32", lambda: W.random_sparse(4000, 16000, seed=30), 600, True, 32, 4),
     ("rand_ratio_k13", lambda: W.random_sparse(3001, 12000, seed=23), 500, False, 13, 5),
     ("rand_normalized_k1", lambda: W.random_sparse(2500, 9000, seed=24), 400, True, 1, 5),
     ("knn_ratio", lambda: W.knn_gmm(4000, 8, 1, 6, 25), 250, False, 8, 10),
