@@ -60,6 +60,9 @@ def _load():
         "oracle_coarsen": (I, [I64, I64, P, P, P, P, I64, P, P, P, P]),
         "oracle_loss": (I, [I64, I64, P, P, P, I64, I64, P, P, P, P, I, P, I, D, P, P, P, P]),
         "oracle_shifted_jacobi": (I, [I64, I64, P, P, P, I, P, I, D, I, P]),
+        "oracle_colour": (I, [I64, I64, P, P, U64, P, P]),
+        "oracle_gs_sweeps": (I, [I64, I64, P, P, P, I, P, I, D, P]),
+        "oracle_smooth_gs": (I, [I64, I64, P, P, P, I, I, D, U64, I, U64, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -255,6 +258,46 @@ def compose_maps(levels):
     for lv in levels[1:]:
         out = lv.agg[out].astype(np.int64)
     return out.astype(np.int32)
+
+
+# --------------------------------------------------------------------------
+# Multicolour Gauss-Seidel smoothing (the relaxation named in Sec. 3.2.1)
+# --------------------------------------------------------------------------
+def colour(n, u, v, seed=0):
+    """Greedy colouring in descending SplitMix64 priority (oracle_colour)."""
+    lib = _load()
+    u, v = _i32(u), _i32(v)
+    out = np.empty(n, np.int32)
+    nc = ctypes.c_int32(0)
+    _check(lib.oracle_colour(n, len(u), _p(u), _p(v), ctypes.c_uint64(seed), _p(out), ctypes.byref(nc)), "colour")
+    return out, int(nc.value)
+
+
+def gs_order(colours):
+    """Nodes in ascending (colour, id)."""
+    colours = np.asarray(colours)
+    return np.lexsort((np.arange(len(colours)), colours)).astype(np.int64)
+
+
+def gs_sweeps(n, u, v, w, X, order, sweeps=1, omega=0.7):
+    """Bare Gauss-Seidel sweeps in the given node order (no normalisation)."""
+    X = np.array(X, dtype=np.float64, order="C", copy=True)
+    order = np.ascontiguousarray(order, dtype=np.int64)
+    lib = _load()
+    u, v, w = _i32(u), _i32(v), _f64(w)
+    _check(lib.oracle_gs_sweeps(n, len(u), _p(u), _p(v), _p(w), X.shape[1], _p(order), int(sweeps), float(omega),
+                                _p(X)), "gs_sweeps")
+    return X
+
+
+def smooth_gs(n, u, v, w, K, sweeps, omega=0.7, seed=0, level=0, colour_seed=0):
+    """Test vectors smoothed by multicolour Gauss-Seidel (oracle_smooth_gs)."""
+    lib = _load()
+    u, v, w = _i32(u), _i32(v), _f64(w)
+    X = np.empty((n, K), np.float64)
+    _check(lib.oracle_smooth_gs(n, len(u), _p(u), _p(v), _p(w), K, sweeps, float(omega), ctypes.c_uint64(seed),
+                                level, ctypes.c_uint64(colour_seed), _p(X)), "smooth_gs")
+    return X
 
 
 # --------------------------------------------------------------------------

@@ -565,3 +565,192 @@ int oracle_shifted_jacobi(int64_t n, int64_t m, const int32_t* u, const int32_t*
     free(acc);
     return st;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Multicolour Gauss-Seidel (the relaxation Sec. 3.2.1 names).  The paper     */
+/* gives no ordering; reading: a greedy colouring in descending priority,      */
+/* priority of node i = (output number c+1 of SplitMix64 seeded with `seed`,   */
+/* c = 2^62 + i; then the larger id wins a tie), each node taking the smallest */
+/* colour not used by its already-coloured neighbours.  A sweep then visits    */
+/* the nodes in ascending (colour, id).                                        */
+/* ------------------------------------------------------------------------ */
+static uint64_t or_prio(uint64_t seed, int64_t i) {
+    return oracle_splitmix64(seed, ((uint64_t)1 << 62) + (uint64_t)i);
+}
+
+typedef struct {
+    uint64_t p;
+    int64_t i;
+} or_prio_node;
+
+static int or_cmp_prio_desc(const void* x, const void* y) {
+    const or_prio_node* a = (const or_prio_node*)x;
+    const or_prio_node* b = (const or_prio_node*)y;
+    if (a->p != b->p) return a->p > b->p ? -1 : 1;
+    return a->i > b->i ? -1 : (a->i < b->i ? 1 : 0);
+}
+
+/* adjacency lists in ascending edge id (= ascending neighbour id): nbr/wt of
+ * node i at [ptr[i], ptr[i+1]) */
+static int or_adjacency(int64_t n, int64_t m, const int32_t* u, const int32_t* v, const double* w, int64_t** ptr_out,
+                        int32_t** nbr_out, double** wt_out) {
+    int64_t* ptr = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+    int64_t* fill = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+    int32_t* nbr = (int32_t*)malloc(sizeof(int32_t) * (size_t)(2 * m > 0 ? 2 * m : 1));
+    double* wt = (double*)malloc(sizeof(double) * (size_t)(2 * m > 0 ? 2 * m : 1));
+    if (!ptr || !fill || !nbr || !wt) {
+        free(ptr);
+        free(fill);
+        free(nbr);
+        free(wt);
+        return OR_ENOMEM;
+    }
+    for (int64_t e = 0; e < m; ++e) {
+        ptr[u[e] + 1]++;
+        ptr[v[e] + 1]++;
+    }
+    for (int64_t i = 0; i < n; ++i) ptr[i + 1] += ptr[i];
+    /* edges in ascending id; for node i the edges (q, i), q < i, come before
+       the edges (i, r), and each group is in ascending id */
+    for (int64_t e = 0; e < m; ++e) {
+        int64_t p = u[e], q = v[e];
+        int64_t sq = ptr[q] + fill[q]++;
+        nbr[sq] = (int32_t)p;
+        wt[sq] = w ? w[e] : 0.0;
+    }
+    for (int64_t e = 0; e < m; ++e) {
+        int64_t p = u[e], q = v[e];
+        int64_t sp = ptr[p] + fill[p]++;
+        nbr[sp] = (int32_t)q;
+        wt[sp] = w ? w[e] : 0.0;
+    }
+    free(fill);
+    *ptr_out = ptr;
+    *nbr_out = nbr;
+    *wt_out = wt;
+    return OR_OK;
+}
+
+int oracle_colour(int64_t n, int64_t m, const int32_t* u, const int32_t* v, uint64_t seed, int32_t* colour,
+                  int32_t* ncolours) {
+    int64_t* ptr;
+    int32_t* nbr;
+    double* wt;
+    int st = or_adjacency(n, m, u, v, NULL, &ptr, &nbr, &wt);
+    if (st != OR_OK) return st;
+    or_prio_node* order = (or_prio_node*)malloc(sizeof(or_prio_node) * (size_t)(n > 0 ? n : 1));
+    unsigned char* used = (unsigned char*)calloc((size_t)n + 2, 1);
+    if (!order || !used) {
+        free(order);
+        free(used);
+        free(ptr);
+        free(nbr);
+        free(wt);
+        return OR_ENOMEM;
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        order[i].p = or_prio(seed, i);
+        order[i].i = i;
+        colour[i] = -1;
+    }
+    qsort(order, (size_t)n, sizeof(or_prio_node), or_cmp_prio_desc);
+    int32_t nc = 0;
+    for (int64_t t = 0; t < n; ++t) {
+        int64_t i = order[t].i;
+        for (int64_t j = ptr[i]; j < ptr[i + 1]; ++j)
+            if (colour[nbr[j]] >= 0) used[colour[nbr[j]]] = 1;
+        int32_t c = 0;
+        while (used[c]) ++c;
+        colour[i] = c;
+        if (c + 1 > nc) nc = c + 1;
+        for (int64_t j = ptr[i]; j < ptr[i + 1]; ++j)
+            if (colour[nbr[j]] >= 0) used[colour[nbr[j]]] = 0;
+    }
+    *ncolours = nc;
+    free(order);
+    free(used);
+    free(ptr);
+    free(nbr);
+    free(wt);
+    return OR_OK;
+}
+
+/* One Gauss-Seidel sweep x_i <- (1 - theta) x_i + theta (sum_j w_ij x_j) / D(i,i)
+ * over the nodes in the given order, each update seeing the latest values;
+ * neighbour sums in ascending edge id; an isolated node keeps its value. */
+static void or_gs_sweep(int64_t n, const int64_t* ptr, const int32_t* nbr, const double* wt, const double* deg,
+                        const int64_t* order, int K, double omega, double* X, double* acc) {
+    for (int64_t t = 0; t < n; ++t) {
+        int64_t i = order[t];
+        if (!(deg[i] > 0.0)) continue;
+        for (int k = 0; k < K; ++k) acc[k] = 0.0;
+        for (int64_t j = ptr[i]; j < ptr[i + 1]; ++j)
+            for (int k = 0; k < K; ++k) acc[k] += wt[j] * X[(int64_t)nbr[j] * K + k];
+        for (int k = 0; k < K; ++k) X[i * K + k] = (1.0 - omega) * X[i * K + k] + omega * (acc[k] / deg[i]);
+    }
+}
+
+typedef struct {
+    int32_t c;
+    int64_t i;
+} or_colour_node;
+
+static int or_cmp_colour_id(const void* x, const void* y) {
+    const or_colour_node* a = (const or_colour_node*)x;
+    const or_colour_node* b = (const or_colour_node*)y;
+    if (a->c != b->c) return a->c < b->c ? -1 : 1;
+    return a->i < b->i ? -1 : (a->i > b->i ? 1 : 0);
+}
+
+/* `sweeps` Gauss-Seidel sweeps in the given node order (n entries), no
+ * normalisation: the bare relaxation, for pins */
+int oracle_gs_sweeps(int64_t n, int64_t m, const int32_t* u, const int32_t* v, const double* w, int K,
+                     const int64_t* order, int sweeps, double omega, double* X) {
+    int64_t* ptr;
+    int32_t* nbr;
+    double* wt;
+    int st = or_adjacency(n, m, u, v, w, &ptr, &nbr, &wt);
+    if (st != OR_OK) return st;
+    double* deg = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double* acc = (double*)malloc(sizeof(double) * (size_t)K);
+    if (!deg || !acc) st = OR_ENOMEM;
+    if (st == OR_OK) st = oracle_degrees(n, m, u, v, w, deg);
+    for (int s = 0; st == OR_OK && s < sweeps; ++s) or_gs_sweep(n, ptr, nbr, wt, deg, order, K, omega, X, acc);
+    free(deg);
+    free(acc);
+    free(ptr);
+    free(nbr);
+    free(wt);
+    return st;
+}
+
+/* Test-vector smoothing with multicolour Gauss-Seidel: X0 as for Alg. 3,
+ * centre + normalise, then `sweeps` times one sweep in (colour, id) order of
+ * the colouring seeded with `colour_seed`, followed by centre + normalise. */
+int oracle_smooth_gs(int64_t n, int64_t m, const int32_t* u, const int32_t* v, const double* w, int K, int sweeps,
+                     double omega, uint64_t seed, int level, uint64_t colour_seed, double* X) {
+    int32_t* colour = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    or_colour_node* cn = (or_colour_node*)malloc(sizeof(or_colour_node) * (size_t)(n > 0 ? n : 1));
+    int64_t* order = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    int32_t nc = 0;
+    int st = (colour && cn && order) ? OR_OK : OR_ENOMEM;
+    if (st == OR_OK) st = oracle_colour(n, m, u, v, colour_seed, colour, &nc);
+    if (st == OR_OK) {
+        for (int64_t i = 0; i < n; ++i) {
+            cn[i].c = colour[i];
+            cn[i].i = i;
+        }
+        qsort(cn, (size_t)n, sizeof(or_colour_node), or_cmp_colour_id);
+        for (int64_t t = 0; t < n; ++t) order[t] = cn[t].i;
+        oracle_test_vectors_raw(n, K, seed, level, X);
+        oracle_center_normalize(n, K, X);
+        for (int s = 0; st == OR_OK && s < sweeps; ++s) {
+            st = oracle_gs_sweeps(n, m, u, v, w, K, order, 1, omega, X);
+            oracle_center_normalize(n, K, X);
+        }
+    }
+    free(colour);
+    free(cn);
+    free(order);
+    return st;
+}

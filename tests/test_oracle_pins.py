@@ -25,8 +25,8 @@ GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 def test_laplacian_zero_row_sums_and_structure(oracle_mod):
     g = W.random_sparse(40, 120, seed=1)
     L = oracle_mod.dense_laplacian(g.n, g.u, g.v, g.w)
-    assert np.allclose(L.sum(1), 0.0, atol=1e-13)
-    assert np.allclose(L, L.T, atol=0)
+    assert np.allclose(L.sum(1), 0.0, rtol=0, atol=1e-13)
+    assert np.allclose(L, L.T, rtol=0, atol=0)
     off = L - np.diag(np.diag(L))
     assert (off <= 0).all()
     # diagonal is the weighted degree: every weight counted at both endpoints
@@ -47,16 +47,16 @@ def test_spectrum_path_cycle_complete_star(oracle_mod, n):
     j = np.arange(n)
     g = W.path(n)
     ev = np.linalg.eigvalsh(oracle_mod.dense_laplacian(g.n, g.u, g.v, g.w))
-    assert np.allclose(ev, np.sort(4 * np.sin(np.pi * j / (2 * n)) ** 2), atol=1e-12)
+    assert np.allclose(ev, np.sort(4 * np.sin(np.pi * j / (2 * n)) ** 2), rtol=0, atol=1e-12)
     g = W.cycle(n)
     ev = np.linalg.eigvalsh(oracle_mod.dense_laplacian(g.n, g.u, g.v, g.w))
-    assert np.allclose(ev, np.sort(4 * np.sin(np.pi * j / n) ** 2), atol=1e-12)
+    assert np.allclose(ev, np.sort(4 * np.sin(np.pi * j / n) ** 2), rtol=0, atol=1e-12)
     g = W.complete(n, weight=1.5)
     ev = np.linalg.eigvalsh(oracle_mod.dense_laplacian(g.n, g.u, g.v, g.w))
-    assert np.allclose(ev, [0.0] + [1.5 * n] * (n - 1), atol=1e-12)
+    assert np.allclose(ev, [0.0] + [1.5 * n] * (n - 1), rtol=0, atol=1e-12)
     g = W.star(n)
     ev = np.linalg.eigvalsh(oracle_mod.dense_laplacian(g.n, g.u, g.v, g.w))
-    assert np.allclose(ev, [0.0] + [1.0] * (n - 2) + [float(n)], atol=1e-12)
+    assert np.allclose(ev, [0.0] + [1.0] * (n - 2) + [float(n)], rtol=0, atol=1e-12)
 
 
 def test_spectrum_grid(oracle_mod):
@@ -65,7 +65,7 @@ def test_spectrum_grid(oracle_mod):
     ev = np.linalg.eigvalsh(oracle_mod.dense_laplacian(g.n, g.u, g.v, g.w))
     i, j = np.meshgrid(np.arange(a), np.arange(b))
     ref = np.sort((4 * np.sin(np.pi * i / (2 * a)) ** 2 + 4 * np.sin(np.pi * j / (2 * b)) ** 2).ravel())
-    assert np.allclose(ev, ref, atol=1e-12)
+    assert np.allclose(ev, ref, rtol=0, atol=1e-12)
 
 
 # ---------------------------------------------------------------------------
@@ -93,7 +93,7 @@ def test_test_vectors_distribution(oracle_mod):
 def test_center_normalize(oracle_mod):
     X = oracle_mod.center_normalize(oracle_mod.test_vectors_raw(1000, 5, 7, 0))
     assert np.all(np.abs(X.sum(0)) <= 1e-13 * np.sqrt(1000))
-    assert np.allclose((X * X).sum(0), 1.0, atol=1e-14)
+    assert np.allclose((X * X).sum(0), 1.0, rtol=0, atol=1e-14)
 
 
 # ---------------------------------------------------------------------------
@@ -178,7 +178,7 @@ def test_sweep_isolated_node_unchanged(oracle_mod):
     Y = oracle_mod.jacobi_sweep(6, u, v, w, X, 0.7)
     assert np.array_equal(Y[5], X[5])
     # an interior path node: (1-w) x_i + w (x_{i-1} + x_{i+1}) / 2
-    assert np.allclose(Y[2], 0.3 * X[2] + 0.7 * (X[1] + X[3]) / 2)
+    assert np.allclose(Y[2], 0.3 * X[2] + 0.7 * (X[1] + X[3]) / 2, rtol=0, atol=1e-15)
 
 
 def test_smooth_invariants_and_lowpass(oracle_mod):
@@ -189,7 +189,7 @@ def test_smooth_invariants_and_lowpass(oracle_mod):
     for S in range(1, 6):
         X = oracle_mod.smooth(g.n, g.u, g.v, g.w, K, S, 0.7, 0, 0)
         assert np.all(np.abs(X.sum(0)) <= 1e-13 * np.sqrt(g.n))
-        assert np.allclose((X * X).sum(0), 1.0, atol=1e-14)
+        assert np.allclose((X * X).sum(0), 1.0, rtol=0, atol=1e-14)
         LX = oracle_mod.laplacian_apply(g.n, g.u, g.v, g.w, X)
         rq.append(float(np.mean((X * LX).sum(0))))
     # low-pass filter (Sec. 3.5): the Rayleigh quotient falls with every sweep
@@ -209,8 +209,8 @@ def test_affinity_hand_examples(oracle_mod):
     u = np.array([0, 2, 3, 0], np.int32)
     v = np.array([1, 3, 4, 5], np.int32)
     d, a = oracle_mod.affinity(6, u, v, X, want_a=True)
-    assert np.allclose(a, [0.5, 0.0, 1.0, 0.0], atol=1e-15)
-    assert np.allclose(d, [0.5, 1.0, 0.0, 1.0], atol=1e-15)
+    assert np.allclose(a, [0.5, 0.0, 1.0, 0.0], rtol=0, atol=1e-15)
+    assert np.allclose(d, [0.5, 1.0, 0.0, 1.0], rtol=0, atol=1e-15)
     assert d[2] == 0.0
 
 
@@ -431,21 +431,21 @@ def test_eig_solver_closed_forms(oracle_mod):
     g = W.cycle(50)
     ev = oracle_mod.smallest_nontrivial_eigs(g.n, g.u, g.v, g.w, 6)
     ref = np.sort(4 * np.sin(np.pi * np.arange(50) / 50) ** 2)[1:7]
-    assert np.allclose(ev, ref, atol=1e-12)
+    assert np.allclose(ev, ref, rtol=0, atol=1e-12)
     # two components: two zeros skipped
     u = np.concatenate([W.path(10).u, W.path(10).u + 10]).astype(np.int32)
     v = np.concatenate([W.path(10).v, W.path(10).v + 10]).astype(np.int32)
     ev = oracle_mod.smallest_nontrivial_eigs(20, u, v, np.ones(18), 4)
     jj = np.arange(1, 10)
     ref = np.sort(np.repeat(4 * np.sin(np.pi * jj / 20) ** 2, 2))[:4]
-    assert np.allclose(ev, ref, atol=1e-12)
+    assert np.allclose(ev, ref, rtol=0, atol=1e-12)
     # 3-D mesh: sums of three 4 sin^2 terms
     g = W.mesh3d(5, 4, 3)
     g.w[:] = 1.0
     ev = oracle_mod.smallest_nontrivial_eigs(g.n, g.u, g.v, g.w, 5)
     t = [4 * np.sin(np.pi * np.arange(k) / (2 * k)) ** 2 for k in (5, 4, 3)]
     ref = np.sort((t[0][None, None, :] + t[1][None, :, None] + t[2][:, None, None]).ravel())[1:6]
-    assert np.allclose(ev, ref, atol=1e-12)
+    assert np.allclose(ev, ref, rtol=0, atol=1e-12)
 
 
 # ---------------------------------------------------------------------------
@@ -599,13 +599,13 @@ def test_coarsest_eigenpairs_closed_forms(oracle_mod):
     n = 30
     p = W.path(n)
     lam, U = oracle_mod.coarsest_eigenpairs(p.n, p.u, p.v, p.w, 6, False)
-    assert np.allclose(lam, 4 * np.sin(np.pi * np.arange(6) / (2 * n)) ** 2, atol=1e-12)
-    assert np.allclose(U.T @ U, np.eye(6), atol=1e-12)
+    assert np.allclose(lam, 4 * np.sin(np.pi * np.arange(6) / (2 * n)) ** 2, rtol=0, atol=1e-12)
+    assert np.allclose(U.T @ U, np.eye(6), rtol=0, atol=1e-12)
     # normalised cut on a regular graph: the spectrum divides by the degree
     c = _cycle_weighted(20, 2.0)
     lam_n, Un = oracle_mod.coarsest_eigenpairs(c.n, c.u, c.v, c.w, 5, True)
     lam_r, _ = oracle_mod.coarsest_eigenpairs(c.n, c.u, c.v, c.w, 5, False)
-    assert np.allclose(lam_n, lam_r / 4.0, atol=1e-12)
+    assert np.allclose(lam_n, lam_r / 4.0, rtol=0, atol=1e-12)
 
 
 def test_coarsest_eigenpairs_generalized_against_lapack(oracle_mod):
@@ -615,25 +615,25 @@ def test_coarsest_eigenpairs_generalized_against_lapack(oracle_mod):
     D = np.diag(np.diag(L))
     lam, U = oracle_mod.coarsest_eigenpairs(g.n, g.u, g.v, g.w, 8, True)
     ref = eigh(L, D, eigvals_only=True)[:8]
-    assert np.allclose(lam, ref, atol=1e-11)
+    assert np.allclose(lam, ref, rtol=0, atol=1e-11)
     assert np.max(np.abs(L @ U - (D @ U) * lam)) <= 1e-10
-    assert np.allclose(U.T @ D @ U, np.eye(8), atol=1e-10)  # B-orthonormal
+    assert np.allclose(U.T @ D @ U, np.eye(8), rtol=0, atol=1e-10)  # B-orthonormal
 
 
 def test_gram_schmidt_properties(oracle_mod):
     rng = np.random.default_rng(13)
     A = rng.normal(size=(50, 6))
     Q = oracle_mod.gram_schmidt(A)
-    assert np.allclose(Q.T @ Q, np.eye(6), atol=1e-12)
+    assert np.allclose(Q.T @ Q, np.eye(6), rtol=0, atol=1e-12)
     # column order: span(Q[:, :j]) = span(A[:, :j]) for every j, and the
     # first column is the first input column normalised
     for j in range(1, 7):
         P = Q[:, :j] @ Q[:, :j].T
-        assert np.allclose(P @ A[:, :j], A[:, :j], atol=1e-10)
-    assert np.allclose(Q[:, 0], A[:, 0] / np.linalg.norm(A[:, 0]))
+        assert np.allclose(P @ A[:, :j], A[:, :j], rtol=0, atol=1e-10)
+    assert np.allclose(Q[:, 0], A[:, 0] / np.linalg.norm(A[:, 0]), rtol=0, atol=1e-15)
     # numpy's QR gives the same factor up to column signs
     Qr, _ = np.linalg.qr(A)
-    assert np.allclose(np.abs(np.sum(Qr * Q, 0)), 1.0, atol=1e-10)
+    assert np.allclose(np.abs(np.sum(Qr * Q, 0)), 1.0, rtol=0, atol=1e-10)
 
 
 def test_multilevel_eigensolve_single_level_is_exact(oracle_mod):
@@ -642,7 +642,7 @@ def test_multilevel_eigensolve_single_level_is_exact(oracle_mod):
     U, lam = oracle_mod.multilevel_eigensolve([(p.n, p.u, p.v, p.w)], [], 5)
     L = oracle_mod.dense_laplacian(p.n, p.u, p.v, p.w)
     rq = np.sum(U * (L @ U), 0)
-    assert np.allclose(rq, 4 * np.sin(np.pi * np.arange(5) / (2 * n)) ** 2, atol=1e-12)
+    assert np.allclose(rq, 4 * np.sin(np.pi * np.arange(5) / (2 * n)) ** 2, rtol=0, atol=1e-12)
 
 
 def test_multilevel_eigensolve_prolongation_and_refinement(oracle_mod):
@@ -655,8 +655,8 @@ def test_multilevel_eigensolve_prolongation_and_refinement(oracle_mod):
     uc, vc, wc = oracle_mod.coarsen(p.n, p.u, p.v, p.w, agg, n // 2)
     graphs = [(p.n, p.u, p.v, p.w), (n // 2, uc, vc, wc)]
     U0, lam = oracle_mod.multilevel_eigensolve(graphs, [agg], 4, iters=0)
-    assert np.allclose(U0[0::2], U0[1::2], atol=0)
-    assert np.allclose(U0.T @ U0, np.eye(4), atol=1e-12)
+    assert np.allclose(U0[0::2], U0[1::2], rtol=0, atol=0)
+    assert np.allclose(U0.T @ U0, np.eye(4), rtol=0, atol=1e-12)
     L = oracle_mod.dense_laplacian(p.n, p.u, p.v, p.w)
     U1, _ = oracle_mod.multilevel_eigensolve(graphs, [agg], 4, iters=20)
     exact = 4 * np.sin(np.pi * np.arange(4) / (2 * n)) ** 2
@@ -665,7 +665,7 @@ def test_multilevel_eigensolve_prolongation_and_refinement(oracle_mod):
     # the first column stays the constant vector (shift 0 fixes it), so every
     # later column is orthogonal to it and, by Courant-Fischer, its Rayleigh
     # quotient is at least the second eigenvalue
-    assert np.allclose(U1[:, 0], U1[0, 0], atol=1e-12)
+    assert np.allclose(U1[:, 0], U1[0, 0], rtol=0, atol=1e-12)
     assert np.all(rq0[1:] >= exact[1] - 1e-12) and np.all(rq1[1:] >= exact[1] - 1e-12)
     assert np.all(np.abs(rq1[1:] - exact[1:]) < np.abs(rq0[1:] - exact[1:]))
 
@@ -680,10 +680,10 @@ def test_reduce_features_against_dense_product(oracle_mod):
     F = rng.normal(size=(n, d))
     P = np.zeros((n, nc))
     P[np.arange(n), agg] = 1.0
-    assert np.allclose(oracle_mod.reduce_features(agg, nc, F), P.T @ F, atol=1e-12)
+    assert np.allclose(oracle_mod.reduce_features(agg, nc, F), P.T @ F, rtol=0, atol=1e-12)
     # mean: (P^T P)^-1 P^T F
     M = np.diag(1.0 / np.diag(P.T @ P))
-    assert np.allclose(oracle_mod.reduce_features(agg, nc, F, mean=True), M @ P.T @ F, atol=1e-12)
+    assert np.allclose(oracle_mod.reduce_features(agg, nc, F, mean=True), M @ P.T @ F, rtol=0, atol=1e-12)
 
 
 def test_reduce_features_invariants(oracle_mod):
@@ -696,3 +696,78 @@ def test_reduce_features_invariants(oracle_mod):
     assert np.array_equal(oracle_mod.reduce_features(np.arange(n, dtype=np.int32), n, Fi), Fi)
     c = np.full((n, 2), 2.5)
     assert np.array_equal(oracle_mod.reduce_features(agg, nc, c, mean=True), np.full((nc, 2), 2.5))
+
+
+# ---------------------------------------------------------------------------
+# Multicolour Gauss-Seidel (Sec. 3.2.1): colouring and sweeps
+# ---------------------------------------------------------------------------
+def _prio(oracle_mod, n, seed):
+    return np.array([oracle_mod.splitmix64(seed, (1 << 62) + i) for i in range(n)], dtype=np.uint64)
+
+
+@pytest.mark.parametrize("seed", [0, 7])
+def test_colouring_is_greedy_and_proper(oracle_mod, seed):
+    from colouring_ref import jones_plassmann
+    for g in (W.random_sparse(300, 1500, seed=51), W.grid2d(12, 9), W.star(30), W.complete(12, 1.0),
+              W.mesh3d(6, 5, 4, seed=52)):
+        col, nc = oracle_mod.colour(g.n, g.u, g.v, seed)
+        assert np.all(col[g.u] != col[g.v])
+        deg = np.bincount(np.concatenate([g.u, g.v]), minlength=g.n)
+        assert nc == col.max() + 1 and nc <= deg.max() + 1
+        assert np.array_equal(col, jones_plassmann(g.n, g.u, g.v, _prio(oracle_mod, g.n, seed)))
+
+
+def _sor_dense(oracle_mod, g, X, order, omega):
+    """One sweep in matrix form: with A split by the visiting order into the
+    part already updated (lower) and the rest (upper),
+    (D - omega A_low) x_new = ((1 - omega) D + omega A_up) x_old."""
+    from scipy.linalg import solve_triangular
+    L = oracle_mod.dense_laplacian(g.n, g.u, g.v, g.w)
+    D = np.diag(L).copy()
+    A = np.diag(D) - L
+    pos = np.empty(g.n, np.int64)
+    pos[order] = np.arange(g.n)
+    Ap = A[np.ix_(order, order)]
+    low, up = np.tril(Ap, -1), np.triu(Ap, 1)
+    Dp = np.diag(D[order])
+    rhs = ((1 - omega) * Dp + omega * up) @ X[order]
+    Xn = solve_triangular(Dp - omega * low, rhs, lower=True)
+    out = np.empty_like(X)
+    out[order] = Xn
+    return out
+
+
+@pytest.mark.parametrize("omega", [1.0, 0.7])
+def test_gs_sweep_matrix_form(oracle_mod, omega):
+    g = W.random_sparse(60, 250, seed=53)
+    rng = np.random.default_rng(54)
+    X = rng.normal(size=(g.n, 3))
+    col, _ = oracle_mod.colour(g.n, g.u, g.v, 3)
+    for order in (oracle_mod.gs_order(col), np.arange(g.n), rng.permutation(g.n)):
+        got = oracle_mod.gs_sweeps(g.n, g.u, g.v, g.w, X, order, 1, omega)
+        assert np.allclose(got, _sor_dense(oracle_mod, g, X, np.asarray(order), omega), rtol=0, atol=1e-12)
+
+
+def test_gs_fixes_constants_and_colour_classes_are_independent(oracle_mod):
+    g = W.mesh3d(5, 4, 3, seed=55)
+    c = np.full((g.n, 2), 3.25)
+    col, _ = oracle_mod.colour(g.n, g.u, g.v, 1)
+    order = oracle_mod.gs_order(col)
+    assert np.allclose(oracle_mod.gs_sweeps(g.n, g.u, g.v, g.w, c, order, 3), c, rtol=0, atol=1e-14)
+    # inside one colour the visiting order does not matter: reversing the ids
+    # within every colour class gives the same sweep, bit for bit
+    rev = np.lexsort((-np.arange(g.n), col)).astype(np.int64)
+    X = np.random.default_rng(56).normal(size=(g.n, 4))
+    assert np.array_equal(oracle_mod.gs_sweeps(g.n, g.u, g.v, g.w, X, order, 2),
+                          oracle_mod.gs_sweeps(g.n, g.u, g.v, g.w, X, rev, 2))
+
+
+def test_smooth_gs_invariants(oracle_mod):
+    g = W.random_sparse(200, 900, seed=57)
+    X = oracle_mod.smooth_gs(g.n, g.u, g.v, g.w, 6, 4, 0.7, 3, 1, 5)
+    assert np.allclose(X.sum(0), 0.0, rtol=0, atol=1e-12) and np.allclose((X * X).sum(0), 1.0, rtol=0, atol=1e-12)
+    # the low-pass effect (Sec. 3.2.1): Rayleigh quotients fall below those of
+    # the raw centred vectors
+    L = oracle_mod.dense_laplacian(g.n, g.u, g.v, g.w)
+    X0 = oracle_mod.smooth_gs(g.n, g.u, g.v, g.w, 6, 0, 0.7, 3, 1, 5)
+    assert np.all(np.sum(X * (L @ X), 0) < np.sum(X0 * (L @ X0), 0))
