@@ -448,6 +448,43 @@ def main():
                "lambda_coarsest": [float(x) for x in lam], "rayleigh": [float(x) for x in rq]}
         del U, hier, lve, Ge
 
+    # Multicolour Gauss-Seidel smoothing (Sec. 3.2.1) on the fine graph:
+    # colouring time (first call), and per sweep (S = 8 minus S = 0) with its
+    # roofline.  Bytes per sweep: the CSR slots, row pointers and the block
+    # read and written once by the colour-class kernels (as the Jacobi sweep),
+    # plus the statistics read and the in-place scaling of the block.
+    gsm = None
+    if rank == 0 and world == 1 and not args.no_eigen:
+        Gg = gr.graph_reduce_create(g.n, u_d, v_d, w_d)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, ncol = gr.graph_reduce_colour(Gg, 0)
+        t_col = (time.perf_counter() - t0) * 1000.0
+        Xg = torch.empty(g.n, wl.K, dtype={"f64": torch.float64, "f32": torch.float32,
+                                           "bf16": torch.bfloat16}[wl.precision], device=dev)
+
+        def tgs(S, reps=3):
+            gr.graph_reduce_smooth_gs(Gg, Xg, S, wl.omega, 0, 0, 0)
+            ts = []
+            for _ in range(reps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                gr.graph_reduce_smooth_gs(Gg, Xg, S, wl.omega, 0, 0, 0)
+                e1.record()
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            return min(ts)
+
+        per = (tgs(8) - tgs(0)) / 8
+        gbytes = sweep_bytes(g.n, g.m, wl.K, xbytes, wbytes) + 3 * g.n * wl.K * xbytes
+        gach = gbytes / (per / 1000.0) / 1e9 if per > 0 else 0.0
+        gsm = {"colours": ncol, "colouring_ms": t_col, "ms_per_sweep": per,
+               "jacobi_ms_per_sweep_level0": all_stats[-1][0]["t_sweeps"] / max(wl.sweeps, 1),
+               "roofline": {"bound": "hbm", "achieved": gach, "peak": peak, "unit": "GB/s", "frac": gach / peak,
+                            "bytes_per_sweep": gbytes}}
+        del Xg, Gg
+
     # Reduced data set F_R = P^T F (Alg. 6, step 4) over the bench step's
     # levels: 16 FP32 features per fine node.  Algorithmic bytes: F read
     # once, F_R written once, the per-level maps read once.
@@ -492,6 +529,7 @@ def main():
                              % (g.m * 16 / 1e6, g.m * 2 * 24 / 1e6)},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "fp32_vs_fp64": cmp64, "multilevel_eigensolver": eig, "reduced_dataset": rdata,
+            "gauss_seidel": gsm,
             "clocks": clocks, "levels": per_level,
         }
         print(json.dumps(line), flush=True)

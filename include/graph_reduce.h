@@ -108,6 +108,25 @@ gr_status graph_reduce_smooth(gr_ctx* ctx, int K, int sweeps, double omega, uint
 gr_status graph_reduce_smooth_noalloc(gr_ctx* ctx, int K, int sweeps, double omega,
                                       uint64_t seed, int level, gr_prec prec, void* X);
 
+/* Test-vector smoothing with the Gauss-Seidel relaxation Sec. 3.2.1 names,
+ * made parallel by a multicolour ordering.  The paper gives no ordering; this
+ * one is the greedy colouring in descending priority (priority of node i =
+ * output number c+1 of SplitMix64 seeded with colour_seed, c = 2^62 + i, the
+ * larger id winning a tie), each node taking the smallest colour unused by its
+ * higher-priority neighbours; a sweep visits the nodes in ascending (colour,
+ * id), each update x_i <- (1-omega) x_i + omega (D^-1 A x)_i seeing the latest
+ * values (nodes of one colour are never adjacent, so a colour is updated at
+ * once).  X0, the centring and normalisation after every sweep, and K, prec
+ * and X are as for graph_reduce_smooth.  The ordering is computed on first use
+ * for a colour_seed and kept in the context. */
+gr_status graph_reduce_smooth_gs(gr_ctx* ctx, int K, int sweeps, double omega, uint64_t seed, int level,
+                                 uint64_t colour_seed, gr_prec prec, void* X);
+
+/* The colouring behind graph_reduce_smooth_gs.
+ *   colour_out     device, n colours in [0, ncolours)
+ *   ncolours_out   host */
+gr_status graph_reduce_colour(gr_ctx* ctx, uint64_t colour_seed, int32_t* colour_out, int32_t* ncolours_out);
+
 /* Per-edge affinity a = (X_p,X_q)^2 / ((X_p,X_p)(X_q,X_q)) (Eq. eqn:agg) and
  * algebraic distance d = 1 - a (Sec. 3.2.2), for every edge (p, q) of the
  * canonical list.  d is evaluated without cancellation as

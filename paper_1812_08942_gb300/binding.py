@@ -22,6 +22,7 @@ _STATUS = {1: "GR_EINVAL", 2: "GR_ENOMEM", 3: "GR_ECUDA", 4: "GR_ETIMEOUT", 5: "
 
 EXPORTED = [
     "graph_reduce_create", "graph_reduce_get_info", "graph_reduce_smooth", "graph_reduce_smooth_noalloc",
+    "graph_reduce_smooth_gs", "graph_reduce_colour",
     "graph_reduce_affinity",
     "graph_reduce_aggregate", "graph_reduce_coarsen", "graph_reduce_get_edges", "graph_reduce_get_map",
     "graph_reduce_multilevel", "graph_reduce_compose_maps", "graph_reduce_eigensolve", "graph_reduce_reduce_data", "graph_reduce_loss_fwd",
@@ -69,6 +70,8 @@ def load():
         "graph_reduce_get_info": (I, [P, ctypes.POINTER(I64), ctypes.POINTER(I64)]),
         "graph_reduce_smooth": (I, [P, I, I, D, U64, I, I, P]),
         "graph_reduce_smooth_noalloc": (I, [P, I, I, D, U64, I, I, P]),
+        "graph_reduce_smooth_gs": (I, [P, I, I, D, U64, I, U64, I, P]),
+        "graph_reduce_colour": (I, [P, U64, P, ctypes.POINTER(I32)]),
         "graph_reduce_affinity": (I, [P, P, I, I, P, P]),
         "graph_reduce_aggregate": (I, [P, P, I, I64, I, I64, P, ctypes.POINTER(I64), ctypes.POINTER(I64)]),
         "graph_reduce_coarsen": (I, [P, P, I64, PP]),
@@ -169,6 +172,24 @@ def graph_reduce_smooth(g: Graph, X, sweeps, omega=0.7, seed=0, level=0):
                                     _prec_of(X.dtype), _ptr(X))
     _check(st, g.handle)
     return X
+
+
+def graph_reduce_smooth_gs(g: Graph, X, sweeps, omega=0.7, seed=0, level=0, colour_seed=0):
+    """Fill X like graph_reduce_smooth, with multicolour Gauss-Seidel sweeps."""
+    assert X.is_cuda and X.is_contiguous() and X.dim() == 2 and X.shape[0] == g.n
+    st = load().graph_reduce_smooth_gs(g.handle, int(X.shape[1]), int(sweeps), float(omega), int(seed), int(level),
+                                       int(colour_seed), _prec_of(X.dtype), _ptr(X))
+    _check(st, g.handle)
+    return X
+
+
+def graph_reduce_colour(g: Graph, colour_seed=0):
+    """Returns (colour int32 tensor on the device, number of colours)."""
+    out = torch.empty(g.n, dtype=torch.int32, device=g.device)
+    nc = ctypes.c_int32(0)
+    st = load().graph_reduce_colour(g.handle, int(colour_seed), _ptr(out), ctypes.byref(nc))
+    _check(st, g.handle)
+    return out, int(nc.value)
 
 
 def graph_reduce_smooth_noalloc(g: Graph, X, sweeps, omega=0.7, seed=0, level=0):

@@ -126,6 +126,25 @@ gr_status graph_reduce_smooth(gr_ctx* ctx, int K, int sweeps, double omega, uint
     return smooth_impl(ctx, K, sweeps, omega, seed, level, prec, X);
 }
 
+gr_status graph_reduce_smooth_gs(gr_ctx* ctx, int K, int sweeps, double omega, uint64_t seed, int level,
+                                 uint64_t colour_seed, gr_prec prec, void* X) {
+    if (!ctx) return set_error(nullptr, GR_EINVAL, "smooth_gs: ctx is NULL");
+    if (!valid_K(K)) return set_error(ctx, GR_EINVAL, "smooth_gs: K must be 4, 8, 16, 24 or 32");
+    if (sweeps < 0 || !(omega > 0.0 && omega <= 1.0))
+        return set_error(ctx, GR_EINVAL, "smooth_gs: need sweeps >= 0 and 0 < omega <= 1");
+    if (level < 0 || level >= (1 << 20)) return set_error(ctx, GR_EINVAL, "smooth_gs: level out of range");
+    if (!X || !aligned16(X)) return set_error(ctx, GR_EINVAL, "smooth_gs: X must be a 16-byte aligned device pointer");
+    if (prec != GR_F64 && prec != GR_F32 && prec != GR_BF16)
+        return set_error(ctx, GR_EINVAL, "smooth_gs: bad precision");
+    return smooth_gs_impl(ctx, K, sweeps, omega, seed, level, colour_seed, prec, X);
+}
+
+gr_status graph_reduce_colour(gr_ctx* ctx, uint64_t colour_seed, int32_t* colour_out, int32_t* ncolours_out) {
+    if (!ctx) return set_error(nullptr, GR_EINVAL, "colour: ctx is NULL");
+    if (!colour_out || !ncolours_out) return set_error(ctx, GR_EINVAL, "colour: NULL output");
+    return colour_impl(ctx, colour_seed, colour_out, ncolours_out);
+}
+
 gr_status graph_reduce_affinity(gr_ctx* ctx, const void* X, int K, gr_prec prec, void* d_out, void* a_out) {
     if (!ctx) return set_error(nullptr, GR_EINVAL, "affinity: ctx is NULL");
     if (!valid_K(K)) return set_error(ctx, GR_EINVAL, "affinity: K must be 4, 8, 16, 24 or 32");
@@ -326,7 +345,7 @@ void graph_reduce_destroy(gr_ctx* c) {
     if (!c) return;
     cudaStream_t s = c->stream;
     void* ptrs[] = {c->eu, c->ev, c->ew, c->eptr, c->rowptr, c->col, c->eid, c->cw32, c->wn64, c->deg,
-                    c->parent_map, c->wpart, c->cw64};
+                    c->parent_map, c->wpart, c->cw64, c->gs_order};
     for (void* p : ptrs)
         if (p) cudaFreeAsync(p, s);
     c->ws.release();

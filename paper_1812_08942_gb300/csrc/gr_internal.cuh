@@ -43,7 +43,7 @@ enum WsSlot {
     WS_AGG_STATE, WS_AGG_LIST, WS_AGG_KEYS, WS_AGG_SMALL,
     WS_COARSE_KEYS, WS_COARSE_VALS, WS_COARSE_TMP,
     WS_GAL_KEYS, WS_GAL_UCOL, WS_GAL_UW, WS_GAL_ROWS,
-    WS_EIG, WS_EIG_WORK, WS_DATASET,
+    WS_EIG, WS_EIG_WORK, WS_DATASET, WS_GS,
     WS_LOSS_A, WS_LOSS_B, WS_LOSS_C,
     WS_ML_X, WS_ML_D, WS_ML_AGG,
     WS_PINNED_UNUSED,
@@ -73,6 +73,12 @@ struct gr_ctx {
     int32_t* wpart = nullptr;
     int64_t wpart_W = 0;
     int4* cw64 = nullptr;       // 2m: (col, 0, w / deg_row as FP64), built on first FP64 sweep
+    // multicolour Gauss-Seidel ordering for one colouring seed, built on first use:
+    // nodes in ascending (colour, id) and each colour's range in that list
+    int32_t* gs_order = nullptr;
+    std::vector<int64_t> gs_ptr;
+    uint64_t gs_seed = 0;
+    bool gs_ready = false;
     // mapping from the parent level (coarse contexts only)
     int32_t* parent_map = nullptr;
     int64_t parent_n = 0;
@@ -136,6 +142,9 @@ __device__ __forceinline__ int32_t warp_slot(bool keep, int32_t* count) {
 gr_status smooth_impl(gr_ctx* c, int K, int sweeps, double omega, uint64_t seed, int level,
                       gr_prec prec, void* X, cudaEvent_t ev_begin = nullptr,
                       cudaEvent_t ev_end = nullptr);
+gr_status smooth_gs_impl(gr_ctx* c, int K, int sweeps, double omega, uint64_t seed, int level,
+                         uint64_t colour_seed, gr_prec prec, void* X);
+gr_status colour_impl(gr_ctx* c, uint64_t colour_seed, int32_t* colour_out, int32_t* ncolours_out);
 gr_status affinity_impl(gr_ctx* c, const void* X, int K, gr_prec prec, void* d, void* a);
 gr_status aggregate_impl(gr_ctx* c, const void* d, int d_is_f64, int64_t target_nc, int passes,
                          int64_t max_proposals, int32_t* agg, int64_t* nc_out, int64_t* proposals_out);

@@ -825,6 +825,319 @@ gr_status smooth_impl(gr_ctx* c, int K, int sweeps, double omega, uint64_t seed,
     return GR_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Multicolour Gauss-Seidel (the relaxation Sec. 3.2.1 names).  Ordering: the
+// greedy colouring in descending priority, computed by Jones-Plassmann rounds
+// (an uncoloured node whose priority beats all its uncoloured neighbours takes
+// the smallest colour its coloured neighbours leave free).  Adjacent nodes
+// never colour in the same round, and a node's coloured neighbours when it
+// colours are exactly its higher-priority ones, so the result is the greedy
+// colouring whatever the order of the updates within a round.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t gs_prio(uint64_t seed, int64_t i) {
+    return splitmix64_at(seed, (1ull << 62) + (uint64_t)i);
+}
+
+__global__ void k_jp_round(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                           uint64_t seed, int32_t* colour, int32_t* __restrict__ left, int32_t* __restrict__ maxc) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || __ldcg(colour + i) >= 0) return;
+    const uint64_t pi = gs_prio(seed, i);
+    const int64_t b = rowptr[i], e = rowptr[i + 1];
+    for (int64_t j = b; j < e; ++j) {
+        const int32_t q = col[j];
+        if (__ldcg(colour + q) < 0) {
+            const uint64_t pq = gs_prio(seed, q);
+            if (pq > pi || (pq == pi && q > i)) {
+                atomicAdd(left, 1);
+                return;
+            }
+        }
+    }
+    // smallest colour not used by a coloured neighbour, 64 candidates at a time
+    int32_t c = 0;
+    for (int32_t base = 0;; base += 64) {
+        unsigned long long used = 0;
+        for (int64_t j = b; j < e; ++j) {
+            const int32_t cq = __ldcg(colour + col[j]);
+            if (cq >= base && cq < base + 64) used |= 1ull << (cq - base);
+        }
+        if (~used) {
+            c = base + __ffsll((long long)~used) - 1;
+            break;
+        }
+    }
+    colour[i] = c;
+    atomicMax(maxc, c);
+}
+
+__global__ void k_colour_keys(int64_t n, const int32_t* __restrict__ colour, uint32_t* __restrict__ keys,
+                              uint32_t* __restrict__ vals, int32_t* __restrict__ cnt) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    keys[i] = (uint32_t)colour[i];
+    vals[i] = (uint32_t)i;
+    atomicAdd(&cnt[colour[i]], 1);
+}
+
+// Colouring for colour_seed: colour (device, n) and, in the context, the node
+// list in ascending (colour, id) with each colour's range.
+static gr_status gs_prepare(gr_ctx* c, uint64_t colour_seed, int32_t* colour_out) {
+    const int64_t n = c->n;
+    cudaStream_t s = c->stream;
+    size_t need = 0;
+    auto add = [&](size_t bytes) {
+        size_t off = need;
+        need += (bytes + 255) & ~size_t(255);
+        return off;
+    };
+    const size_t o_col = add(4 * (size_t)n), o_k0 = add(4 * (size_t)n), o_v0 = add(4 * (size_t)n),
+                 o_k1 = add(4 * (size_t)n), o_v1 = add(4 * (size_t)n), o_cnt = add(4 * (size_t)(n + 2)),
+                 o_ptr = add(4 * (size_t)(n + 2)), o_ctr = add(64);
+    void* base;
+    GR_TRY_CUDA(c, c->ws.get(WS_GS, need, &base), "colouring scratch");
+    char* B = (char*)base;
+    int32_t* colour = colour_out ? colour_out : (int32_t*)(B + o_col);
+    uint32_t* k0 = (uint32_t*)(B + o_k0);
+    uint32_t* v0 = (uint32_t*)(B + o_v0);
+    uint32_t* k1 = (uint32_t*)(B + o_k1);
+    uint32_t* v1 = (uint32_t*)(B + o_v1);
+    int32_t* cnt = (int32_t*)(B + o_cnt);
+    int32_t* cptr = (int32_t*)(B + o_ptr);
+    int32_t* ctr = (int32_t*)(B + o_ctr);  // [0] left after the round, [1] largest colour
+    int64_t* hs = host_scratch();
+    if (!hs) return set_error(c, GR_ENOMEM, "colouring: pinned scratch unavailable");
+    GR_TRY_CUDA(c, cudaMemsetAsync(colour, 0xff, 4 * (size_t)n, s), "memset");
+    GR_TRY_CUDA(c, cudaMemsetAsync(ctr, 0, 64, s), "memset");
+    const unsigned gn = (unsigned)ceil_div(n > 0 ? n : 1, 256);
+    // every round colours at least the highest-priority uncoloured node
+    int64_t left = n;
+    for (int64_t round = 0; left > 0; ++round) {
+        if (round > n) return set_error(c, GR_ECUDA, "colouring: no progress");
+        GR_TRY_CUDA(c, cudaMemsetAsync(ctr, 0, 4, s), "memset");
+        k_jp_round<<<gn, 256, 0, s>>>(n, c->rowptr, c->col, colour_seed, colour, ctr, ctr + 1);
+        count_launch();
+        GR_TRY_CUDA(c, cudaMemcpyAsync(hs, ctr, 8, cudaMemcpyDeviceToHost, s), "readback");
+        GR_TRY_CUDA(c, cudaStreamSynchronize(s), "sync");
+        const int64_t now = ((int32_t*)hs)[0];
+        if (now >= left) return set_error(c, GR_ECUDA, "colouring: a round made no progress");
+        left = now;
+    }
+    const int32_t ncol = n > 0 ? ((int32_t*)hs)[1] + 1 : 0;
+    // the nodes in ascending (colour, id): a stable sort of the ids by colour
+    GR_TRY_CUDA(c, cudaMemsetAsync(cnt, 0, 4 * (size_t)(ncol + 1), s), "memset");
+    if (n > 0) {
+        k_colour_keys<<<gn, 256, 0, s>>>(n, colour, k0, v0, cnt);
+        count_launch();
+    }
+    int alt = 0;
+    GR_TRY_CUDA(c, radix_sort_u32(k0, v0, k1, v1, n, bits_for((uint64_t)(ncol > 1 ? ncol - 1 : 1)), c->ws, s, &alt),
+                "sort by colour");
+    GR_TRY_CUDA(c, scan_exclusive_i32(cnt, cptr, ncol + 1, c->ws, s), "scan");
+    if (!c->gs_order) GR_TRY_CUDA(c, cudaMallocAsync(&c->gs_order, 4 * (size_t)(n > 0 ? n : 1), s), "alloc");
+    GR_TRY_CUDA(c, cudaMemcpyAsync(c->gs_order, alt ? v1 : v0, 4 * (size_t)n, cudaMemcpyDeviceToDevice, s), "copy");
+    std::vector<int32_t> hp((size_t)ncol + 1);
+    GR_TRY_CUDA(c, cudaMemcpyAsync(hp.data(), cptr, 4 * (size_t)(ncol + 1), cudaMemcpyDeviceToHost, s), "readback");
+    GR_TRY_CUDA(c, cudaStreamSynchronize(s), "sync");
+    c->gs_ptr.assign(hp.begin(), hp.end());
+    c->gs_seed = colour_seed;
+    c->gs_ready = true;
+    return GR_OK;
+}
+
+gr_status colour_impl(gr_ctx* c, uint64_t colour_seed, int32_t* colour_out, int32_t* ncolours_out) {
+    gr_status st = gs_prepare(c, colour_seed, colour_out);
+    if (st != GR_OK) return st;
+    *ncolours_out = (int32_t)c->gs_ptr.size() - 1;
+    return GR_OK;
+}
+
+// Update the listed rows (one colour) in place: G lanes per row, one chunk
+// each; the neighbours have other colours and are not written by this launch.
+template <typename T, int K>
+__global__ void __launch_bounds__(SM_THREADS) k_gs_class(int64_t cnt, const int32_t* __restrict__ rows,
+                                                         const int64_t* __restrict__ rowptr,
+                                                         const typename SlotOf<T>::type* __restrict__ slots,
+                                                         T* __restrict__ X, double omega_d) {
+    using Slot = typename SlotOf<T>::type;
+    using L = RowLayout<T, K>;
+    using Acc = typename AccOf<T>::type;
+    constexpr int E = L::E, G = L::G, RPW = 32 / G;
+    const int lane = threadIdx.x & 31, seg = lane / G, q = lane % G;
+    if (seg >= RPW) return;
+    const int64_t r = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * RPW + seg;
+    if (r >= cnt) return;
+    const int64_t i = rows[r];
+    const int64_t b = rowptr[i], e = rowptr[i + 1];
+    const Acc omega = (Acc)omega_d, one_m = (Acc)(1.0 - omega_d);
+    Acc xi[E];
+    load_chunk<T, E>(X + i * K + q * E, xi);
+    if (b == e) return;  // isolated: keeps its value
+    Acc acc[E];
+#pragma unroll
+    for (int t = 0; t < E; ++t) acc[t] = Acc(0);
+    for (int64_t j = b; j < e; j += 2) {
+        const bool two = j + 1 < e;
+        const Slot v0 = __ldg(slots + j);
+        const Slot v1 = __ldg(slots + (two ? j + 1 : j));
+        Acc x0[E], x1[E];
+        load_chunk<T, E>(X + (int64_t)slot_col(v0) * K + q * E, x0);
+        load_chunk<T, E>(X + (int64_t)slot_col(v1) * K + q * E, x1);
+        const Acc w0 = slot_w(v0, Acc(0)), w1 = slot_w(v1, Acc(0));
+#pragma unroll
+        for (int t = 0; t < E; ++t) {
+            acc[t] = fma(w0, x0[t], acc[t]);
+            if (two) acc[t] = fma(w1, x1[t], acc[t]);
+        }
+    }
+    Acc y[E];
+#pragma unroll
+    for (int t = 0; t < E; ++t) y[t] = one_m * xi[t] + omega * acc[t];
+    store_chunk<T, E>(X + i * K + q * E, y);
+}
+
+// column sums and sums of squares of X (FP64 per-block partials, last-block finish)
+template <typename T, int K>
+__global__ void __launch_bounds__(SM_THREADS) k_col_stats(int64_t n, const T* __restrict__ A, double* __restrict__ part,
+                                                          unsigned* __restrict__ counter,
+                                                          double* __restrict__ stats_out) {
+    using L = RowLayout<T, K>;
+    using Acc = typename AccOf<T>::type;
+    constexpr int E = L::E, G = L::G, GP = L::GP;
+    constexpr int RPW = 32 / GP;
+    const int lane = threadIdx.x & 31;
+    const int q = lane % GP, seg = lane / GP;
+    Acc s1[E], s2[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) s1[e] = s2[e] = Acc(0);
+    const int64_t warp_global = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r0 = warp_global * RPW; r0 < n; r0 += nwarps * RPW) {
+        const int64_t row = r0 + seg;
+        if (row < n && q < G) {
+            Acc x[E];
+            load_chunk<T, E>(A + row * K + q * E, x);
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                s1[e] += x[e];
+                s2[e] += x[e] * x[e];
+            }
+        }
+    }
+    block_stats<Acc, K, E, G, GP>(s1, s2, part, counter, n, stats_out);
+}
+
+// X = (X - mu) * inv_s in place, chunk-parallel (one pointer, plain loads)
+template <typename T, int K>
+__global__ void k_scale_inplace(int64_t n, T* X, const double* __restrict__ stats) {
+    using L = RowLayout<T, K>;
+    using Acc = typename AccOf<T>::type;
+    constexpr int E = L::E, G = L::G;
+    __shared__ Acc st[2 * K];
+    for (int i = threadIdx.x; i < 2 * K; i += blockDim.x) st[i] = (Acc)stats[i];
+    __syncthreads();
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * G) return;
+    const int64_t row = idx / G;
+    const int q = (int)(idx % G);
+    T* p = X + row * K + q * E;
+    Acc x[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) x[e] = (Acc)p[e];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int k = q * E + e;
+        x[e] = (x[e] - st[k]) * st[K + k];
+    }
+    store_chunk<T, E>(p, x);
+}
+
+template <typename T, int K>
+static gr_status run_smooth_gs(gr_ctx* c, int sweeps, double omega, uint64_t seed, int level, uint64_t colour_seed,
+                               T* X) {
+    if (!c->gs_ready || c->gs_seed != colour_seed) {
+        gr_status st = gs_prepare(c, colour_seed, nullptr);
+        if (st != GR_OK) return st;
+    }
+    cudaStream_t s = c->stream;
+    const int64_t n = c->n;
+    constexpr int G = RowLayout<T, K>::G, GP = RowLayout<T, K>::GP;
+    void *p_st, *p_part;
+    GR_TRY_CUDA(c, c->ws.get(WS_SMOOTH_STATS, sizeof(double) * 4 * K + 64, &p_st), "scratch");
+    double* st = (double*)p_st;
+    unsigned* counter = (unsigned*)(st + 4 * K);
+    const int init_rows = SM_WARPS * (32 / GP);
+    const int64_t cap = (int64_t)c->num_sms * 8;
+    const int64_t iwant = ceil_div(n, init_rows);
+    const int igrid = (int)(iwant < cap ? (iwant > 0 ? iwant : 1) : cap);
+    GR_TRY_CUDA(c, c->ws.get(WS_SMOOTH_PART, sizeof(double) * 2 * K * (size_t)igrid, &p_part), "scratch");
+    double* part = (double*)p_part;
+    GR_TRY_CUDA(c, cudaMemsetAsync(counter, 0, sizeof(unsigned), s), "memset");
+    const typename SlotOf<T>::type* slots;
+    if constexpr (sizeof(T) == 8) {
+        if (!c->cw64) {
+            GR_TRY_CUDA(c, cudaMallocAsync(&c->cw64, sizeof(int4) * (size_t)(2 * c->m > 0 ? 2 * c->m : 1), s),
+                        "alloc");
+            if (c->m > 0) {
+                k_pack64<<<(unsigned)ceil_div(2 * c->m, 256), 256, 0, s>>>(2 * c->m, c->col, c->wn64, c->cw64);
+                count_launch();
+            }
+        }
+        slots = c->cw64;
+    } else {
+        slots = c->cw32;
+    }
+    const unsigned ga = (unsigned)ceil_div(n * G > 0 ? n * G : 1, 256);
+    // X0, centred and normalised
+    k_init<T, K><<<igrid, SM_THREADS, 0, s>>>(n, seed, (uint64_t)level, X, part, counter, st);
+    count_launch();
+    if (n > 0) {
+        k_scale_inplace<T, K><<<ga, 256, 0, s>>>(n, X, st);
+        count_launch();
+    }
+    constexpr int RPB = SM_WARPS * (32 / G);  // rows per block in k_gs_class
+    for (int it = 0; it < sweeps; ++it) {
+        for (size_t col = 0; col + 1 < c->gs_ptr.size(); ++col) {
+            const int64_t b = c->gs_ptr[col], cnt = c->gs_ptr[col + 1] - b;
+            if (cnt <= 0) continue;
+            k_gs_class<T, K><<<(unsigned)ceil_div(cnt, RPB), SM_THREADS, 0, s>>>(cnt, c->gs_order + b, c->rowptr,
+                                                                                slots, X, omega);
+            count_launch();
+        }
+        k_col_stats<T, K><<<igrid, SM_THREADS, 0, s>>>(n, X, part, counter, st);
+        count_launch();
+        if (n > 0) {
+            k_scale_inplace<T, K><<<ga, 256, 0, s>>>(n, X, st);
+            count_launch();
+        }
+    }
+    GR_TRY_CUDA(c, cudaGetLastError(), "gauss-seidel kernels");
+    return GR_OK;
+}
+
+template <typename T>
+static gr_status smooth_gs_typed(gr_ctx* c, int K, int sweeps, double omega, uint64_t seed, int level,
+                                 uint64_t colour_seed, void* X) {
+    switch (K) {
+        case 4: return run_smooth_gs<T, 4>(c, sweeps, omega, seed, level, colour_seed, (T*)X);
+        case 8: return run_smooth_gs<T, 8>(c, sweeps, omega, seed, level, colour_seed, (T*)X);
+        case 16: return run_smooth_gs<T, 16>(c, sweeps, omega, seed, level, colour_seed, (T*)X);
+        case 24: return run_smooth_gs<T, 24>(c, sweeps, omega, seed, level, colour_seed, (T*)X);
+        case 32: return run_smooth_gs<T, 32>(c, sweeps, omega, seed, level, colour_seed, (T*)X);
+    }
+    return set_error(c, GR_EINVAL, "smooth_gs: unsupported K");
+}
+
+gr_status smooth_gs_impl(gr_ctx* c, int K, int sweeps, double omega, uint64_t seed, int level,
+                         uint64_t colour_seed, gr_prec prec, void* X) {
+    switch (prec) {
+        case GR_F64: return smooth_gs_typed<double>(c, K, sweeps, omega, seed, level, colour_seed, X);
+        case GR_F32: return smooth_gs_typed<float>(c, K, sweeps, omega, seed, level, colour_seed, X);
+        case GR_BF16: return smooth_gs_typed<__nv_bfloat16>(c, K, sweeps, omega, seed, level, colour_seed, X);
+        default: return set_error(c, GR_EINVAL, "smooth_gs: unknown precision");
+    }
+}
+
 }  // namespace gr
 
 // ---------------------------------------------------------------------------
