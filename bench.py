@@ -39,7 +39,7 @@ SAMPLE_DIV = 8
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
@@ -127,7 +127,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
             return
@@ -136,9 +136,11 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
 
-    def stop(self):
+    def stop(self, window=None):
+        """Clock summary of the samples that arrived inside `window` (host
+        perf_counter times around the timed region; all samples if none did)."""
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -150,7 +152,11 @@ class ClockSampler:
             self.thread.join(timeout=2)
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        lines = self.lines
+        inside = [x for x in lines if window[0] <= x[0] <= window[1]] if window is not None else []
+        if inside:
+            lines = inside
+        for _, ln in lines:
             parts = [x.strip() for x in ln.split(",")]
             if len(parts) < 8:
                 continue
@@ -165,7 +171,7 @@ class ClockSampler:
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "samples_in_timed_region": len(inside)}
 
 
 # ---------------------------------------------------------------------------
@@ -292,6 +298,7 @@ def main():
     launches0 = gr.graph_reduce_launch_count()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
+    t_begin = time.perf_counter()
     ev0.record()
     all_stats = []
     for _ in range(args.steps):
@@ -303,7 +310,8 @@ def main():
     if world > 1:
         dist.barrier()
     launches = gr.graph_reduce_launch_count() - launches0
-    clocks = sampler.stop()
+    t_end = time.perf_counter()
+    clocks = sampler.stop((t_begin, t_end))
     t_ms = ev0.elapsed_time(ev1)
     t_max = max_over_ranks(t_ms, world, dev)
     edges_per_step = sum(s["m"] for s in all_stats[-1])
