@@ -48,7 +48,8 @@ struct AggState {
     int32_t* flags;    // n: label scan input
     int32_t* lab;      // n
     uint64_t* keys;    // 2m per-slot keys (FP32 distances), else unused
-    int32_t* ctr;      // [0] heads, [1] pairs, [2..3] proposals (u64), [4..7] error flags
+    int32_t* ctr;      // [0] heads, [1] pairs, [2..3] proposals (u64), [4..7] error flags,
+                       // [8..11] the same counts of a first pass merged without readback
 };
 
 __global__ void k_agg_init(int64_t n, int32_t* __restrict__ cl, int32_t* __restrict__ nxt,
@@ -387,6 +388,19 @@ __global__ void k_merge(int32_t npairs, const int32_t* __restrict__ pc, const in
     tail[c] = tail[b];
 }
 
+// every pair merges (the pass cannot exceed its merge budget); pair count on the device
+__global__ void k_merge_all(const int32_t* __restrict__ npairs, const int32_t* __restrict__ pc,
+                            const int32_t* __restrict__ pb, int32_t* __restrict__ cl, int32_t* __restrict__ nxt,
+                            int32_t* __restrict__ tail) {
+    const int32_t cnt = *npairs;
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
+        const int32_t c = pc[i], b = pb[i];
+        for (int32_t p = b; p >= 0; p = nxt[p]) cl[p] = c;
+        nxt[tail[c]] = b;
+        tail[c] = tail[b];
+    }
+}
+
 __global__ void k_head_flags(int64_t n, const int32_t* __restrict__ cl, int32_t* __restrict__ flags) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) flags[i] = cl[i] == (int32_t)i ? 1 : 0;
@@ -489,9 +503,12 @@ gr_status aggregate_impl(gr_ctx* c, const void* d, int d_is_f64, int64_t target_
 
     int64_t n_cur = n;
     int64_t total_proposals = 0;
+    // When 2 target <= n the first pass cannot exceed its merge budget (a
+    // matching has at most n/2 pairs), so it merges on the device without a
+    // readback; its counts are checked at the next pass's readback.
+    bool deferred = false;
     for (int pass = 0; pass < passes; ++pass) {
-        if (n_cur <= target_nc) break;
-        const int64_t allowed = n_cur - target_nc;
+        if (!deferred && n_cur <= target_nc) break;
         const bool first = pass == 0;
         GR_TRY_CUDA(c, cudaMemsetAsync(S.ctr, 0, 16, s), "memset");
         if (d_is_f64) k_suitor_init<true><<<gn, 256, 0, s>>>(n, S.cl, S.ws, S.wl, S.ctr + 0, first ? 0 : 1);
@@ -500,19 +517,37 @@ gr_status aggregate_impl(gr_ctx* c, const void* d, int d_is_f64, int64_t target_
         if (d_is_f64) launch_suitor_lpc<true>(c, S, lpc, n_cur, d, chain_cap, first);
         else launch_suitor_lpc<false>(c, S, lpc, n_cur, d, chain_cap, first);
         GR_TRY_CUDA(c, cudaGetLastError(), "aggregate matching");
-        GR_TRY_CUDA(c, cudaMemcpyAsync(hctr, S.ctr, 32, cudaMemcpyDeviceToHost, s), "readback");
+        if (first && passes > 1 && 2 * target_nc <= n_cur) {
+            k_merge_all<<<(unsigned)ceil_div(n / 2 > 0 ? n / 2 : 1, 256), 256, 0, s>>>(S.ctr + 1, S.pc, S.pb, S.cl,
+                                                                                     S.nxt, S.tail);
+            count_launch();
+            // keep this pass's heads, pairs and proposals for the next readback
+            GR_TRY_CUDA(c, cudaMemcpyAsync(S.ctr + 8, S.ctr, 16, cudaMemcpyDeviceToDevice, s), "copy");
+            deferred = true;
+            continue;
+        }
+        GR_TRY_CUDA(c, cudaMemcpyAsync(hctr, S.ctr, 48, cudaMemcpyDeviceToHost, s), "readback");
         GR_TRY_CUDA(c, cudaStreamSynchronize(s), "sync");
-        const int64_t pass_proposals = (int64_t)(((const unsigned long long*)hctr)[1]);
-        total_proposals += pass_proposals;
-        if (proposals_out) *proposals_out = total_proposals;
         if (hctr[4] || hctr[5]) return set_error(c, GR_EINVAL, "aggregate: distances must be >= 0 and not NaN");
         if (hctr[6]) return set_error(c, GR_ECUDA, "aggregate: a proposal chain exceeded its bound");
         if (hctr[7]) return set_error(c, GR_ECUDA, "aggregate: one-sided suitor at termination");
+        if (deferred) {  // the first pass, merged on the device
+            const int64_t p0 = (int64_t)(((const unsigned long long*)hctr)[5]);
+            total_proposals += p0;
+            if (max_proposals > 0 && p0 > max_proposals)
+                return set_error(c, GR_ETIMEOUT, "aggregate: proposal budget exceeded");
+            n_cur -= hctr[9];
+            deferred = false;
+        }
+        const int64_t pass_proposals = (int64_t)(((const unsigned long long*)hctr)[1]);
+        total_proposals += pass_proposals;
+        if (proposals_out) *proposals_out = total_proposals;
         if (!first && hctr[0] != n_cur) return set_error(c, GR_ECUDA, "aggregate: internal cluster count mismatch");
         if (max_proposals > 0 && pass_proposals > max_proposals)
             return set_error(c, GR_ETIMEOUT, "aggregate: proposal budget exceeded");
+        const int64_t allowed = n_cur - target_nc;
         const int32_t npairs = hctr[1];
-        if (npairs == 0) break;
+        if (npairs == 0 || allowed <= 0) break;
         const unsigned gp = (unsigned)ceil_div(npairs, 256);
         if ((int64_t)npairs > allowed) {
             // keep the `allowed` smallest keys: stable sort by lo, then by hi
@@ -548,6 +583,7 @@ gr_status aggregate_impl(gr_ctx* c, const void* d, int d_is_f64, int64_t target_
         k_merge<<<gp, 256, 0, s>>>(npairs, S.pc, S.pb, S.keep, S.cl, S.nxt, S.tail); count_launch();
         GR_TRY_CUDA(c, cudaGetLastError(), "aggregate merge");
     }
+    if (deferred) return set_error(c, GR_ECUDA, "aggregate: internal pass bookkeeping");
     // labels: rank of each cluster head (= its smallest member)
     k_head_flags<<<gn, 256, 0, s>>>(n, S.cl, S.flags); count_launch();
     GR_TRY_CUDA(c, scan_exclusive_i32(S.flags, S.lab, n, c->ws, s), "scan labels");

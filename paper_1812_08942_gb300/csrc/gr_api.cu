@@ -6,6 +6,8 @@
 #include <new>
 #include <string>
 
+#include <vector>
+
 #include "gr_internal.cuh"
 
 namespace gr {
@@ -248,10 +250,9 @@ gr_status graph_reduce_multilevel(gr_ctx* fine, const gr_params* p, gr_ctx** lev
     const size_t xsz = prec == GR_F64 ? 8 : (prec == GR_F32 ? 4 : 2);
     const size_t dsz = prec == GR_F64 ? 8 : 4;
     cudaStream_t s = fine->stream;
-    cudaEvent_t ev[7];
+    // seven events per level, read once after the loop (no per-level wait)
     const bool timed = stats_out != nullptr;
-    if (timed)
-        for (int i = 0; i < 7; ++i) GR_TRY_CUDA(fine, cudaEventCreate(&ev[i]), "event");
+    std::vector<cudaEvent_t> evs;
     gr_ctx* cur = fine;
     gr_status st = GR_OK;
     int nl = 0;
@@ -264,6 +265,19 @@ gr_status graph_reduce_multilevel(gr_ctx* fine, const gr_params* p, gr_ctx** lev
         if (e != cudaSuccess) {
             st = cuda_error(fine, e, "multilevel scratch");
             break;
+        }
+        cudaEvent_t* ev = nullptr;
+        if (timed) {
+            for (int i = 0; i < 7; ++i) {
+                cudaEvent_t e = nullptr;
+                if (cudaEventCreate(&e) != cudaSuccess) {
+                    st = set_error(fine, GR_ECUDA, "multilevel: event");
+                    break;
+                }
+                evs.push_back(e);
+            }
+            if (st != GR_OK) break;
+            ev = &evs[(size_t)7 * lvl];
         }
         if (timed) cudaEventRecord(ev[0], s);
         st = smooth_impl(cur, p->K, p->sweeps, p->omega, p->seed, lvl, prec, px, timed ? ev[5] : nullptr,
@@ -292,26 +306,31 @@ gr_status graph_reduce_multilevel(gr_ctx* fine, const gr_params* p, gr_ctx** lev
             break;
         }
         if (timed) {
-            cudaEventSynchronize(ev[4]);
             gr_level_stats& L = stats_out[nl];
             L.n = cur->n;
             L.m = cur->m;
             L.nc = next->n;
             L.mc = next->m;
             L.proposals = proposals;
-            cudaEventElapsedTime(&L.t_smooth, ev[0], ev[1]);
-            cudaEventElapsedTime(&L.t_affinity, ev[1], ev[2]);
-            cudaEventElapsedTime(&L.t_aggregate, ev[2], ev[3]);
-            cudaEventElapsedTime(&L.t_coarsen, ev[3], ev[4]);
             L.sweeps = p->sweeps;
-            L.t_sweeps = 0.f;
-            if (p->sweeps > 0) cudaEventElapsedTime(&L.t_sweeps, ev[5], ev[6]);
         }
         levels_out[nl++] = next;
         cur = next;
     }
-    if (timed)
-        for (int i = 0; i < 7; ++i) cudaEventDestroy(ev[i]);
+    if (timed) {
+        if (nl > 0) cudaEventSynchronize(evs[(size_t)7 * (nl - 1) + 4]);
+        for (int l = 0; l < nl; ++l) {
+            const cudaEvent_t* ev = &evs[(size_t)7 * l];
+            gr_level_stats& L = stats_out[l];
+            cudaEventElapsedTime(&L.t_smooth, ev[0], ev[1]);
+            cudaEventElapsedTime(&L.t_affinity, ev[1], ev[2]);
+            cudaEventElapsedTime(&L.t_aggregate, ev[2], ev[3]);
+            cudaEventElapsedTime(&L.t_coarsen, ev[3], ev[4]);
+            L.t_sweeps = 0.f;
+            if (p->sweeps > 0) cudaEventElapsedTime(&L.t_sweeps, ev[5], ev[6]);
+        }
+        for (auto& e : evs) cudaEventDestroy(e);
+    }
     *nlevels_out = nl;
     return st;
 }
