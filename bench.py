@@ -411,6 +411,32 @@ def main():
                  "speedup": t64 / (t_max / args.steps), "lambda10_max_rel_err": rel,
                  "at_accuracy": bool(rel <= 1e-3), "aggregates_identical": bool(same_maps),
                  "lambda10_fp64": [float(x) for x in ev[1]]}
+        # BF16 storage of the test vectors (FP32 accumulation), same comparison
+        if prec != gr.GR_BF16:
+            pb = gr.ReduceParams(K=wl.K, sweeps=wl.sweeps, omega=wl.omega, seed=0, prec=gr.GR_BF16, passes=2,
+                                 level_ratio=4, final_target=wl.final_target, max_levels=32)
+            Gb = gr.graph_reduce_create(g.n, u_d, v_d, w_d)
+            lvb, _st = gr.graph_reduce_multilevel(Gb, pb, want_stats=False)
+            del lvb, Gb
+            torch.cuda.synchronize()
+            e0.record()
+            for ib in range(k64):
+                Gb = gr.graph_reduce_create(g.n, u_d, v_d, w_d)
+                lvb, _st = gr.graph_reduce_multilevel(Gb, pb, want_stats=False)
+                if ib < k64 - 1:
+                    del Gb, lvb
+            e1.record()
+            torch.cuda.synchronize()
+            tb = e0.elapsed_time(e1) / k64
+            fu, fv, fw = (t.numpy() for t in gr.graph_reduce_get_edges(lvb[-1], on_host=True))
+            evb = _or.smallest_nontrivial_eigs(lvb[-1].n, fu, fv, fw, 10)
+            relb = float(np.max(np.abs(evb - ev[1]) / np.abs(ev[1])))
+            m0 = gr.graph_reduce_get_map(lvb[0]).cpu().numpy()
+            m64 = gr.graph_reduce_get_map(lv64[0]).cpu().numpy()
+            cmp64["bf16_storage"] = {"ms_per_step": tb, "speedup_vs_fp64": t64 / tb, "lambda10_max_rel_err": relb,
+                                     "at_accuracy": bool(relb <= 1e-3), "levels": len(lvb),
+                                     "level0_map_agreement": float(np.mean(m0 == m64)) if len(m0) == len(m64) else None}
+            del Gb, lvb
         del G32, lv32, G64, lv64
 
     # Multilevel Laplacian eigensolver (Alg. 5) on a deeper reduction of the
@@ -455,6 +481,42 @@ def main():
                                       "frac": ach / peak, "bytes": sm_bytes},
                "lambda_coarsest": [float(x) for x in lam], "rayleigh": [float(x) for x in rq]}
         del U, hier, lve, Ge
+
+    # Spectral-mismatch loss and its adjoint (the differentiable edge-weight
+    # objective): fine graph against the final reduced graph through the
+    # composed map, the FP32 smoothed block of the step's first level,
+    # 5 coarse sweeps; forward and forward + backward times.
+    lossm = None
+    if rank == 0 and world == 1 and not args.no_eigen and prec != gr.GR_F64:
+        Gl = gr.graph_reduce_create(g.n, u_d, v_d, w_d)
+        lvl, _ = gr.graph_reduce_multilevel(Gl, params, want_stats=False)
+        comp = gr.graph_reduce_compose_maps(lvl)
+        Cl = lvl[-1]
+        Xl = torch.empty(g.n, wl.K, dtype=torch.float32, device=dev)
+        gr.graph_reduce_smooth(Gl, Xl, wl.sweeps, wl.omega, 0, 0)
+        _, _, wcl = gr.graph_reduce_get_edges(Cl)
+        wc32 = wcl.float().contiguous()
+
+        def tloss(backward, reps=5):
+            ts = []
+            for _ in range(reps + 1):
+                w = wc32.clone().requires_grad_(backward)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                L = gr.spectral_mismatch_loss(w, Gl, Cl, comp, Xl, 5, wl.omega)
+                if backward:
+                    L.backward()
+                e1.record()
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            return min(ts[1:]), float(L.item())
+
+        t_f, lval = tloss(False)
+        t_fb, _ = tloss(True)
+        lossm = {"fine_n": g.n, "coarse_n": Cl.n, "coarse_m": Cl.m, "K": wl.K, "coarse_sweeps": 5, "loss": lval,
+                 "ms_forward": t_f, "ms_forward_backward": t_fb}
+        del Xl, Cl, lvl, Gl, comp, wc32
 
     # Multicolour Gauss-Seidel smoothing (Sec. 3.2.1) on the fine graph:
     # colouring time (first call), and per sweep (S = 8 minus S = 0) with its
@@ -537,7 +599,7 @@ def main():
                              % (g.m * 16 / 1e6, g.m * 2 * 24 / 1e6)},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "fp32_vs_fp64": cmp64, "multilevel_eigensolver": eig, "reduced_dataset": rdata,
-            "gauss_seidel": gsm,
+            "gauss_seidel": gsm, "spectral_mismatch_loss": lossm,
             "clocks": clocks, "levels": per_level,
         }
         print(json.dumps(line), flush=True)
