@@ -213,6 +213,56 @@ def loss(n, u, v, w, nc, uc, vc, wc, agg, X, sweeps, omega=0.7, want_grad=True):
 
 
 # --------------------------------------------------------------------------
+# Edge-weight scaling of the reduced graph by constrained SGD with momentum
+# (Alg. 1, lines 1-23), driven by the exact gradient of the spectral-mismatch
+# loss.  Readings: L_P is the reduced graph with the weights being scaled and
+# L_G the same graph with its initial weights, so lambda_1 ~ min_p
+# d_G(p) / d_P(p) (Eq. courant-fischer-3) starts at 1; the loss replaces
+# lambda_n as the objective (sensitivity = d loss / d w, step size and
+# convergence test from its ratio and relative decrease); every edge of an
+# iteration updates from the degrees at the iteration's start (the paper
+# gives no edge order); updates never go below zero (the scheme scales up).
+# --------------------------------------------------------------------------
+def scale_edges(n, u, v, w, nc, uc, vc, wc0, agg, X, sweeps=5, omega=0.7, alpha=0.5, eta_max=1.0,
+                delta_bar=0.5, eps=1e-3, kmax=10):
+    """Returns (wc, history): the scaled weights and, per iteration, the loss
+    before its update and the lambda_1 estimate after it."""
+    uc = np.asarray(uc, np.int64)
+    vc = np.asarray(vc, np.int64)
+    wc = np.array(wc0, dtype=np.float64, copy=True)
+    dG = degrees(nc, uc, vc, wc)
+    dP = dG.copy()
+    dw = np.zeros_like(wc)
+    step_delta = delta_bar ** (1.0 / kmax)  # line 1
+    nz = dP > 0
+    lam1 = float(np.min(dG[nz] / dP[nz])) if nz.any() else 1.0
+    eta = eta_max
+    L0 = None
+    L_prev = None
+    history = []
+    for k in range(1, kmax + 1):
+        L, g, _, _ = loss(n, u, v, w, nc, uc, vc, wc, agg, X, sweeps, omega)
+        if L0 is None:
+            L0 = L
+        if L_prev is not None and (L_prev - L) / L < eps:  # line 3
+            break
+        dw = np.maximum(alpha * dw - eta * g, 0.0)  # line 7, scaling up
+        bound = lam1 * step_delta
+        phi_p = dG[uc] / (dP[uc] + dw)  # lines 8-9
+        phi_q = dG[vc] / (dP[vc] + dw)
+        cap = np.minimum(dG[uc] / bound - dP[uc], dG[vc] / bound - dP[vc])  # lines 11-13
+        dw = np.where(np.minimum(phi_p, phi_q) <= bound, np.maximum(cap, 0.0), dw)
+        wc = wc + dw  # lines 15-17
+        dP = degrees(nc, uc, vc, wc)
+        eta = (L / L0) * eta_max  # line 19
+        nz = dP > 0
+        lam1 = float(np.min(dG[nz] / dP[nz])) if nz.any() else 1.0  # line 21
+        history.append((L, lam1))
+        L_prev = L
+    return wc, history
+
+
+# --------------------------------------------------------------------------
 # Level loop (the paper repeats Phase A level by level; Alg. 5 consumes the
 # hierarchy).  Per-level target max(ceil(n/4), final_target).
 # --------------------------------------------------------------------------

@@ -771,3 +771,69 @@ def test_smooth_gs_invariants(oracle_mod):
     L = oracle_mod.dense_laplacian(g.n, g.u, g.v, g.w)
     X0 = oracle_mod.smooth_gs(g.n, g.u, g.v, g.w, 6, 0, 0.7, 3, 1, 5)
     assert np.all(np.sum(X * (L @ X), 0) < np.sum(X0 * (L @ X0), 0))
+
+
+# ---------------------------------------------------------------------------
+# Edge scaling (Alg. 1 driven by the loss gradient)
+# ---------------------------------------------------------------------------
+def _scaling_case(oracle_mod, seed=71):
+    g = W.random_sparse(400, 1600, seed=seed)
+    lv = oracle_mod.reduce_multilevel(g.n, g.u, g.v, g.w, 8, 5, final_target=60)
+    agg = oracle_mod.compose_maps(lv)
+    X = oracle_mod.smooth(g.n, g.u, g.v, g.w, 8, 5)
+    return g, lv[-1], agg, X
+
+
+def test_scale_edges_zero_step_and_monotone(oracle_mod):
+    g, c, agg, X = _scaling_case(oracle_mod)
+    w0, h0 = oracle_mod.scale_edges(g.n, g.u, g.v, g.w, c.nc, c.uc, c.vc, c.wc, agg, X, eta_max=0.0, kmax=5)
+    assert np.array_equal(w0, c.wc) and len(h0) == 1 and h0[0][1] == 1.0
+    w, h = oracle_mod.scale_edges(g.n, g.u, g.v, g.w, c.nc, c.uc, c.vc, c.wc, agg, X, eta_max=5.0, kmax=6, eps=0.0)
+    assert len(h) == 6 and np.all(w >= c.wc) and np.any(w > c.wc)
+    # descent: every update lowered the loss (a flipped gradient sign raises it)
+    losses = [x[0] for x in h] + [oracle_mod.loss(g.n, g.u, g.v, g.w, c.nc, c.uc, c.vc, w, agg, X, 5)[0]]
+    assert all(b < a for a, b in zip(losses, losses[1:]))
+
+
+def test_scale_edges_lambda1_estimate_bounds_the_spectrum(oracle_mod):
+    # Courant-Fischer: d_G(p)/d_P(p) is the quotient of the indicator of p,
+    # whose part orthogonal to 1 has the same quotient, so the estimate is at
+    # least the smallest generalised eigenvalue of (L_G, L_P) on 1-perp
+    from scipy.linalg import eigh, null_space
+    g, c, agg, X = _scaling_case(oracle_mod)
+    w, h = oracle_mod.scale_edges(g.n, g.u, g.v, g.w, c.nc, c.uc, c.vc, c.wc, agg, X, eta_max=20.0, kmax=4, eps=0.0)
+    LG = oracle_mod.dense_laplacian(c.nc, c.uc, c.vc, c.wc)
+    LP = oracle_mod.dense_laplacian(c.nc, c.uc, c.vc, w)
+    Q = null_space(np.ones((1, c.nc)))
+    lam_min = eigh(Q.T @ LG @ Q, Q.T @ LP @ Q, eigvals_only=True)[0]
+    assert h[-1][1] >= lam_min - 1e-12
+    assert lam_min < 1.0  # the scaling moved the spectrum (the check is not vacuous)
+
+
+def test_scale_edges_cap_binds_on_a_matching(oracle_mod):
+    # fine graph: 30 disjoint weighted paths of 4 nodes, aggregates {0,1} and
+    # {2,3} of each path, so the reduced graph is 30 disjoint edges: no two
+    # edges share a node, every update sees the true degrees, and a huge step
+    # is capped so that d_G(p)/d_P(p) equals the bound lambda_1 * Delta
+    # (= delta_bar^(1/kmax) on the first iteration) at every node
+    rng = np.random.default_rng(72)
+    P = 30
+    u = np.concatenate([4 * np.arange(P) + t for t in range(3)]).astype(np.int32)
+    v = u + 1
+    order = np.lexsort((v, u))
+    u, v = u[order], v[order]
+    w = rng.uniform(0.5, 2.0, len(u))
+    n = 4 * P
+    agg = (np.arange(n) // 2).astype(np.int32)
+    uc, vc, wc = oracle_mod.coarsen(n, u, v, w, agg, 2 * P)
+    assert len(uc) == P
+    X = oracle_mod.smooth(n, u, v, w, 4, 2)
+    kmax, delta_bar = 4, 0.3
+    wn, h = oracle_mod.scale_edges(n, u, v, w, 2 * P, uc, vc, wc, agg, X, eta_max=1e9, delta_bar=delta_bar,
+                                   kmax=1, eps=0.0)
+    bound = delta_bar ** (1.0 / 1)
+    assert np.allclose(wc / wn, bound, rtol=0, atol=1e-14) and h[0][1] == pytest.approx(bound, abs=1e-14)
+    wn4, h4 = oracle_mod.scale_edges(n, u, v, w, 2 * P, uc, vc, wc, agg, X, eta_max=1e9, delta_bar=delta_bar,
+                                     kmax=kmax, eps=0.0)
+    step = delta_bar ** (1.0 / kmax)
+    assert np.allclose([x[1] for x in h4], [step ** (k + 1) for k in range(kmax)], rtol=0, atol=1e-13)
