@@ -282,6 +282,30 @@ gr_status graph_reduce_loss_bwd(gr_ctx* coarse, const float* saved, int K, const
                                 int sweeps_c, double omega, const float* grad_loss,
                                 float* grad_w_out);
 
+/* Edge-weight scaling of the reduced graph by constrained SGD with momentum
+ * (Alg. 1; Eqs. formula_weight_sensitivity2, courant-fischer-3),
+ * driven by the exact gradient of the spectral-mismatch loss
+ * (graph_reduce_loss_fwd / _bwd).  Alg. 1 scales a sparsifier P of G; here
+ * L_P is `coarse` with the weights being scaled and L_G the same graph with
+ * the initial weights, so the lambda_1 estimate min_p d_G(p)/d_P(p) starts at
+ * 1.  The loss stands in for lambda_n (which needs a Laplacian solver): its
+ * gradient is the sensitivity, eta_k = (loss_k / loss_1) eta_max, and the loop
+ * stops when (loss_{k-1} - loss_k) / loss_k < eps or after kmax iterations.
+ * Per iteration every edge, from the degrees at the iteration's start (the
+ * paper gives no edge order), takes dw <- max(alpha dw - eta grad, 0); if
+ * min(d_G(p)/(d_P(p)+dw), d_G(q)/(d_P(q)+dw)) <= lambda_1 Delta, with
+ * Delta = delta_bar^(1/kmax), dw is capped to keep that ratio at the bound
+ * (never below 0); w += dw; then d_P and lambda_1 are recomputed.
+ *   agg, X, K, sweeps_c, omega   as for graph_reduce_loss_fwd
+ *   w_inout        device, coarse m FP32: the initial weights in, scaled out
+ *   iters_out      host, iterations that updated the weights
+ *   loss_hist      host, kmax entries or NULL: the loss before each update
+ *   lambda1_hist   host, kmax entries or NULL: lambda_1 after each update */
+gr_status graph_reduce_scale_edges(gr_ctx* fine, gr_ctx* coarse, const int32_t* agg, const float* X, int K,
+                                   int sweeps_c, double omega, double alpha, double eta_max, double delta_bar,
+                                   double eps, int kmax, float* w_inout, int32_t* iters_out, double* loss_hist,
+                                   double* lambda1_hist);
+
 /* Number of kernels this library has launched in the process so far (a
  * diagnostic counter, not tied to any paper passage). */
 uint64_t graph_reduce_launch_count(void);

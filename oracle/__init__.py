@@ -214,7 +214,7 @@ def loss(n, u, v, w, nc, uc, vc, wc, agg, X, sweeps, omega=0.7, want_grad=True):
 
 # --------------------------------------------------------------------------
 # Edge-weight scaling of the reduced graph by constrained SGD with momentum
-# (Alg. 1, lines 1-23), driven by the exact gradient of the spectral-mismatch
+# (Alg. 1), driven by the exact gradient of the spectral-mismatch
 # loss.  Readings: L_P is the reduced graph with the weights being scaled and
 # L_G the same graph with its initial weights, so lambda_1 ~ min_p
 # d_G(p) / d_P(p) (Eq. courant-fischer-3) starts at 1; the loss replaces
@@ -233,7 +233,7 @@ def scale_edges(n, u, v, w, nc, uc, vc, wc0, agg, X, sweeps=5, omega=0.7, alpha=
     dG = degrees(nc, uc, vc, wc)
     dP = dG.copy()
     dw = np.zeros_like(wc)
-    step_delta = delta_bar ** (1.0 / kmax)  # line 1
+    step_delta = delta_bar ** (1.0 / kmax)  # per-iteration share of the bound
     nz = dP > 0
     lam1 = float(np.min(dG[nz] / dP[nz])) if nz.any() else 1.0
     eta = eta_max
@@ -244,19 +244,19 @@ def scale_edges(n, u, v, w, nc, uc, vc, wc0, agg, X, sweeps=5, omega=0.7, alpha=
         L, g, _, _ = loss(n, u, v, w, nc, uc, vc, wc, agg, X, sweeps, omega)
         if L0 is None:
             L0 = L
-        if L_prev is not None and (L_prev - L) / L < eps:  # line 3
+        if L_prev is not None and (L_prev - L) / L < eps:  # convergence test
             break
-        dw = np.maximum(alpha * dw - eta * g, 0.0)  # line 7, scaling up
+        dw = np.maximum(alpha * dw - eta * g, 0.0)  # momentum step, scaling up only
         bound = lam1 * step_delta
-        phi_p = dG[uc] / (dP[uc] + dw)  # lines 8-9
+        phi_p = dG[uc] / (dP[uc] + dw)  # degree ratios after the step
         phi_q = dG[vc] / (dP[vc] + dw)
-        cap = np.minimum(dG[uc] / bound - dP[uc], dG[vc] / bound - dP[vc])  # lines 11-13
+        cap = np.minimum(dG[uc] / bound - dP[uc], dG[vc] / bound - dP[vc])  # lambda_1 guard
         dw = np.where(np.minimum(phi_p, phi_q) <= bound, np.maximum(cap, 0.0), dw)
-        wc = wc + dw  # lines 15-17
+        wc = wc + dw  # weight update
         dP = degrees(nc, uc, vc, wc)
-        eta = (L / L0) * eta_max  # line 19
+        eta = (L / L0) * eta_max  # step size from the loss ratio
         nz = dP > 0
-        lam1 = float(np.min(dG[nz] / dP[nz])) if nz.any() else 1.0  # line 21
+        lam1 = float(np.min(dG[nz] / dP[nz])) if nz.any() else 1.0  # new lambda_1 estimate
         history.append((L, lam1))
         L_prev = L
     return wc, history

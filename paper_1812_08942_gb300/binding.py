@@ -25,7 +25,7 @@ EXPORTED = [
     "graph_reduce_smooth_gs", "graph_reduce_colour",
     "graph_reduce_affinity",
     "graph_reduce_aggregate", "graph_reduce_coarsen", "graph_reduce_get_edges", "graph_reduce_get_map",
-    "graph_reduce_multilevel", "graph_reduce_compose_maps", "graph_reduce_eigensolve", "graph_reduce_reduce_data", "graph_reduce_loss_fwd",
+    "graph_reduce_multilevel", "graph_reduce_compose_maps", "graph_reduce_eigensolve", "graph_reduce_reduce_data", "graph_reduce_scale_edges", "graph_reduce_loss_fwd",
     "graph_reduce_loss_bwd", "graph_reduce_launch_count", "graph_reduce_last_error", "graph_reduce_destroy",
 ]
 
@@ -82,6 +82,7 @@ def load():
         "graph_reduce_compose_maps": (I, [PP, I, P]),
         "graph_reduce_eigensolve": (I, [PP, I, I, I, D, I, P, P, P]),
         "graph_reduce_reduce_data": (I, [PP, I, P, I, I, I, P]),
+        "graph_reduce_scale_edges": (I, [P, P, P, P, I, I, D, D, D, D, D, I, P, ctypes.POINTER(I32), P, P]),
         "graph_reduce_loss_fwd": (I, [P, P, P, P, I, P, I, D, P, P]),
         "graph_reduce_loss_bwd": (I, [P, P, I, P, I, D, P, P]),
         "graph_reduce_launch_count": (ctypes.c_uint64, []),
@@ -358,6 +359,23 @@ def graph_reduce_loss_fwd(fine: Graph, coarse: Graph, agg, X, w_c, sweeps_c, ome
                                       float(omega), _ptr(loss), _ptr(saved))
     _check(st, fine.handle)
     return loss, saved
+
+
+def graph_reduce_scale_edges(fine: Graph, coarse: Graph, agg, X, w_c, sweeps_c=5, omega=0.7, alpha=0.5,
+                             eta_max=1.0, delta_bar=0.5, eps=1e-3, kmax=10):
+    """Scale the reduced graph's FP32 weights w_c in place (Alg. 1 driven by
+    the loss gradient).  Returns (w_c, history) with history a list of
+    (loss before the update, lambda_1 after it) per iteration."""
+    assert X.dtype == torch.float32 and w_c.dtype == torch.float32 and w_c.numel() == coarse.m
+    lh = np.zeros(kmax, np.float64)
+    l1 = np.zeros(kmax, np.float64)
+    it = ctypes.c_int32(0)
+    st = load().graph_reduce_scale_edges(fine.handle, coarse.handle, _ptr(agg), _ptr(X), int(X.shape[1]),
+                                         int(sweeps_c), float(omega), float(alpha), float(eta_max), float(delta_bar),
+                                         float(eps), int(kmax), _ptr(w_c), ctypes.byref(it),
+                                         lh.ctypes.data_as(ctypes.c_void_p), l1.ctypes.data_as(ctypes.c_void_p))
+    _check(st, fine.handle)
+    return w_c, [(float(lh[i]), float(l1[i])) for i in range(it.value)]
 
 
 def graph_reduce_loss_bwd(coarse: Graph, saved, K, w_c, sweeps_c, omega, grad_loss, grad_w=None):

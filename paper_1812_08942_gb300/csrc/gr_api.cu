@@ -354,6 +354,22 @@ gr_status graph_reduce_loss_bwd(gr_ctx* coarse, const float* saved, int K, const
     return loss_bwd_impl(coarse, saved, K, w_c, sweeps_c, omega, grad_loss, grad_w_out);
 }
 
+gr_status graph_reduce_scale_edges(gr_ctx* fine, gr_ctx* coarse, const int32_t* agg, const float* X, int K,
+                                   int sweeps_c, double omega, double alpha, double eta_max, double delta_bar,
+                                   double eps, int kmax, float* w_inout, int32_t* iters_out, double* loss_hist,
+                                   double* lambda1_hist) {
+    if (!fine || !coarse) return set_error(fine, GR_EINVAL, "scale_edges: NULL context");
+    if (!agg || !X || !w_inout) return set_error(fine, GR_EINVAL, "scale_edges: NULL argument");
+    if (!valid_K(K) || sweeps_c < 0 || !(omega > 0.0 && omega <= 1.0))
+        return set_error(fine, GR_EINVAL, "scale_edges: need K in {4,8,16,24,32}, sweeps >= 0, 0 < omega <= 1");
+    if (!(alpha >= 0.0 && alpha < 1.0) || !(eta_max >= 0.0) || !(delta_bar > 0.0 && delta_bar <= 1.0) ||
+        !(eps == eps) || kmax < 1)
+        return set_error(fine, GR_EINVAL, "scale_edges: need 0 <= alpha < 1, eta_max >= 0, 0 < delta_bar <= 1, kmax >= 1");
+    if (coarse->stream != fine->stream) return set_error(fine, GR_EINVAL, "scale_edges: contexts must share a stream");
+    return scale_edges_impl(fine, coarse, agg, X, K, sweeps_c, omega, alpha, eta_max, delta_bar, eps, kmax, w_inout,
+                            iters_out, loss_hist, lambda1_hist);
+}
+
 uint64_t graph_reduce_launch_count(void) { return launch_count(); }
 
 const char* graph_reduce_last_error(const gr_ctx* ctx) {

@@ -43,7 +43,7 @@ enum WsSlot {
     WS_AGG_STATE, WS_AGG_LIST, WS_AGG_KEYS, WS_AGG_SMALL,
     WS_COARSE_KEYS, WS_COARSE_VALS, WS_COARSE_TMP,
     WS_GAL_KEYS, WS_GAL_UCOL, WS_GAL_UW, WS_GAL_ROWS,
-    WS_EIG, WS_EIG_WORK, WS_DATASET, WS_GS,
+    WS_EIG, WS_EIG_WORK, WS_DATASET, WS_GS, WS_SCALE,
     WS_LOSS_A, WS_LOSS_B, WS_LOSS_C,
     WS_ML_X, WS_ML_D, WS_ML_AGG,
     WS_PINNED_UNUSED,
@@ -154,6 +154,9 @@ gr_status reduce_data_impl(gr_ctx* const* levels, int nlevels, const void* F, in
                            void* F_out);
 gr_status eigensolve_impl(gr_ctx* const* levels, int nlevels, int k, int normalized, double omega, int iters,
                           double* U_out, double* lambda_out, double* rayleigh_out);
+gr_status scale_edges_impl(gr_ctx* fine, gr_ctx* coarse, const int32_t* agg, const float* X, int K, int sweeps,
+                           double omega, double alpha, double eta_max, double delta_bar, double eps, int kmax,
+                           float* w, int32_t* iters_out, double* loss_hist, double* lam1_hist);
 gr_status loss_fwd_impl(gr_ctx* fine, gr_ctx* coarse, const int32_t* agg, const float* X, int K,
                         const float* w_c, int sweeps, double omega, float* loss, float* saved);
 gr_status loss_bwd_impl(gr_ctx* coarse, const float* saved, int K, const float* w_c, int sweeps,
