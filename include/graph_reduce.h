@@ -88,6 +88,14 @@ gr_status graph_reduce_get_info(const gr_ctx* ctx, int64_t* n_out, int64_t* m_ou
 gr_status graph_reduce_smooth(gr_ctx* ctx, int K, int sweeps, double omega, uint64_t seed,
                               int level, gr_prec prec, void* X);
 
+/* The random test-vector block X0 of graph_reduce_smooth before any centring
+ * (Sec. 3.2.1: random vectors to be smoothed): entry (i,k) = 2u - 1 as
+ * defined there, rounded once to the storage type (GR_F64: exact; GR_F32:
+ * to nearest, ties to even; GR_BF16: the FP32 value rounded to nearest even).
+ * Arguments as for graph_reduce_smooth; X (device, n x K row-major) is
+ * overwritten. */
+gr_status graph_reduce_test_vectors(gr_ctx* ctx, int K, uint64_t seed, int level, gr_prec prec, void* X);
+
 /* Allocation-free variant of graph_reduce_smooth, for callers that must not
  * allocate device memory once they are running: for example code working
  * inside a fixed, pre-reserved memory budget, or under another framework's

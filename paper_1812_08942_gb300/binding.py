@@ -21,7 +21,8 @@ GR_F64, GR_F32, GR_BF16 = 0, 1, 2
 _STATUS = {1: "GR_EINVAL", 2: "GR_ENOMEM", 3: "GR_ECUDA", 4: "GR_ETIMEOUT", 5: "GR_ESTATE"}
 
 EXPORTED = [
-    "graph_reduce_create", "graph_reduce_get_info", "graph_reduce_smooth", "graph_reduce_smooth_noalloc",
+    "graph_reduce_create", "graph_reduce_get_info", "graph_reduce_test_vectors", "graph_reduce_smooth",
+    "graph_reduce_smooth_noalloc",
     "graph_reduce_smooth_gs", "graph_reduce_colour",
     "graph_reduce_affinity",
     "graph_reduce_aggregate", "graph_reduce_coarsen", "graph_reduce_get_edges", "graph_reduce_get_map",
@@ -68,6 +69,7 @@ def load():
     sig = {
         "graph_reduce_create": (I, [PP, I64, I64, P, P, P, I, P]),
         "graph_reduce_get_info": (I, [P, ctypes.POINTER(I64), ctypes.POINTER(I64)]),
+        "graph_reduce_test_vectors": (I, [P, I, U64, I, I, P]),
         "graph_reduce_smooth": (I, [P, I, I, D, U64, I, I, P]),
         "graph_reduce_smooth_noalloc": (I, [P, I, I, D, U64, I, I, P]),
         "graph_reduce_smooth_gs": (I, [P, I, I, D, U64, I, U64, I, P]),
@@ -171,6 +173,15 @@ def graph_reduce_smooth(g: Graph, X, sweeps, omega=0.7, seed=0, level=0):
     assert X.is_cuda and X.is_contiguous() and X.dim() == 2 and X.shape[0] == g.n
     st = load().graph_reduce_smooth(g.handle, int(X.shape[1]), int(sweeps), float(omega), int(seed), int(level),
                                     _prec_of(X.dtype), _ptr(X))
+    _check(st, g.handle)
+    return X
+
+
+def graph_reduce_test_vectors(g: Graph, X, seed=0, level=0):
+    """Fill X (n x K on the device) with the raw random block before centring."""
+    assert X.is_cuda and X.is_contiguous() and X.dim() == 2 and X.shape[0] == g.n
+    st = load().graph_reduce_test_vectors(g.handle, int(X.shape[1]), int(seed), int(level), _prec_of(X.dtype),
+                                          _ptr(X))
     _check(st, g.handle)
     return X
 

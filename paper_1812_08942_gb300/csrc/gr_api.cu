@@ -128,6 +128,17 @@ gr_status graph_reduce_smooth(gr_ctx* ctx, int K, int sweeps, double omega, uint
     return smooth_impl(ctx, K, sweeps, omega, seed, level, prec, X);
 }
 
+gr_status graph_reduce_test_vectors(gr_ctx* ctx, int K, uint64_t seed, int level, gr_prec prec, void* X) {
+    if (!ctx) return set_error(nullptr, GR_EINVAL, "test_vectors: ctx is NULL");
+    if (!valid_K(K)) return set_error(ctx, GR_EINVAL, "test_vectors: K must be 4, 8, 16, 24 or 32");
+    if (level < 0 || level >= (1 << 20)) return set_error(ctx, GR_EINVAL, "test_vectors: level out of range");
+    if (!X || !aligned16(X))
+        return set_error(ctx, GR_EINVAL, "test_vectors: X must be a 16-byte aligned device pointer");
+    if (prec != GR_F64 && prec != GR_F32 && prec != GR_BF16)
+        return set_error(ctx, GR_EINVAL, "test_vectors: bad precision");
+    return test_vectors_impl(ctx, K, seed, level, prec, X);
+}
+
 gr_status graph_reduce_smooth_gs(gr_ctx* ctx, int K, int sweeps, double omega, uint64_t seed, int level,
                                  uint64_t colour_seed, gr_prec prec, void* X) {
     if (!ctx) return set_error(nullptr, GR_EINVAL, "smooth_gs: ctx is NULL");

@@ -139,6 +139,7 @@ __device__ __forceinline__ int32_t warp_slot(bool keep, int32_t* count) {
 
 // kernels entry points used by the API layer
 // ev_begin / ev_end (optional) are recorded around the sweep kernels only
+gr_status test_vectors_impl(gr_ctx* c, int K, uint64_t seed, int level, gr_prec prec, void* X);
 gr_status smooth_impl(gr_ctx* c, int K, int sweeps, double omega, uint64_t seed, int level,
                       gr_prec prec, void* X, cudaEvent_t ev_begin = nullptr,
                       cudaEvent_t ev_end = nullptr);

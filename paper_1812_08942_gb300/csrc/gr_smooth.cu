@@ -111,24 +111,60 @@ __device__ void block_stats(Acc (&s1)[E], Acc (&s2)[E], double* __restrict__ par
 // Flood 2014), top 53 bits -> u in [0,1), entry 2u - 1, rounded once to the
 // storage type (bfloat16: rounded from the FP32 value).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t c) {
-    uint64_t z = seed + (c + 1ull) * 0x9E3779B97F4A7C15ull;
+constexpr uint64_t SM_GAMMA = 0x9E3779B97F4A7C15ull;
+
+// the generator's output for state z = seed + (c + 1) * gamma
+__device__ __forceinline__ uint64_t splitmix64_mix(uint64_t z) {
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
     return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t c) {
+    return splitmix64_mix(seed + (c + 1ull) * SM_GAMMA);
+}
+
+// 2u - 1 with u = (z>>11) 2^-53 equals t 2^-52 for the integer
+// t = (z>>11) - 2^52, |t| <= 2^52.  This part's FP64 and 64-bit conversion
+// units are slow, so neither conversion below uses them.
+__device__ __forceinline__ int64_t uniform_pm1_int(uint64_t z) { return (int64_t)(z >> 11) - (1ll << 52); }
+
+// FP64: exact, the IEEE bit pattern built with integer operations
+__device__ __forceinline__ double scaled_int_to_f64(int64_t t) {
+    if (t == 0) return 0.0;
+    const uint64_t sign = t < 0 ? (1ull << 63) : 0ull;
+    const uint64_t a = t < 0 ? (uint64_t)(-t) : (uint64_t)t;
+    const int p = 63 - __clzll((long long)a);  // a in [2^p, 2^(p+1)), p <= 52
+    const uint64_t frac = (a << (52 - p)) & ((1ull << 52) - 1ull);
+    return __longlong_as_double((long long)(sign | ((uint64_t)(p - 52 + 1023) << 52) | frac));
+}
+
+// FP32: rounded once to nearest, ties to even, by rounding to odd (Boldo and
+// Melquiond, IEEE Trans. Computers 57(4), 2008).  t = hi 2^29 + lo with
+// 0 <= lo < 2^29; hi 2^29 is exact in FP32, and so is lo rounded to odd on
+// the grid 2^5 (24 significant bits at most).  Their FP32 sum is the nearest
+// even rounding of t whenever that grid lies two bits below t's last kept
+// bit, i.e. |t| >= 2^30; smaller |t| fit in 32 bits and take the 32-bit
+// conversion, which rounds to nearest even itself.
+__device__ __forceinline__ float scaled_int_to_f32(int64_t t) {
+    const int32_t hi = (int32_t)(t >> 29);
+    if ((uint32_t)(hi + 2) > 3u) {  // hi >= 2 or hi <= -3: |t| >= 2^30
+        const uint32_t lo = (uint32_t)t & 0x1fffffffu;
+        const uint32_t lo_odd = (lo & ~31u) | ((lo & 31u) ? 32u : 0u);
+        return (__int2float_rn(hi) * 0x1p29f + __uint2float_rn(lo_odd)) * 0x1p-52f;
+    }
+    return __int2float_rn((int32_t)t) * 0x1p-52f;
 }
 
 template <typename T>
 __device__ __forceinline__ typename AccOf<T>::type uniform_pm1(uint64_t z);
 template <>
 __device__ __forceinline__ double uniform_pm1<double>(uint64_t z) {
-    // 2 * (z>>11) * 2^-53 - 1 = ((z>>11) - 2^52) * 2^-52, exact in FP64
-    return (double)((int64_t)(z >> 11) - (1ll << 52)) * 0x1p-52;
+    return scaled_int_to_f64(uniform_pm1_int(z));
 }
 template <>
 __device__ __forceinline__ float uniform_pm1<float>(uint64_t z) {
-    // one round-to-nearest of the exact value
-    return __ll2float_rn((int64_t)(z >> 11) - (1ll << 52)) * 0x1p-52f;
+    return scaled_int_to_f32(uniform_pm1_int(z));
 }
 template <>
 __device__ __forceinline__ float uniform_pm1<__nv_bfloat16>(uint64_t z) {
@@ -155,10 +191,13 @@ __global__ void __launch_bounds__(SM_THREADS) k_init(int64_t n, uint64_t seed, u
         int64_t row = r0 + seg;
         if (row < n && q < G) {
             Acc x[E];
+            // generator state of this chunk's first entry; the next entries
+            // follow by one gamma each
+            uint64_t zs = seed + ((level << 40) + (uint64_t)row * K + (uint64_t)(q * E) + 1ull) * SM_GAMMA;
 #pragma unroll
             for (int e = 0; e < E; ++e) {
-                uint64_t c = (level << 40) + (uint64_t)row * K + (uint64_t)(q * E + e);
-                x[e] = uniform_pm1<T>(splitmix64_at(seed, c));
+                x[e] = uniform_pm1<T>(splitmix64_mix(zs));
+                zs += SM_GAMMA;
             }
             store_chunk<T, E>(A + row * K + q * E, x);
 #pragma unroll
@@ -810,6 +849,51 @@ static cudaError_t smooth_typed(gr_ctx* c, int K, int sweeps, double omega, uint
         case 32: return run_smooth<T, 32>(c, sweeps, omega, seed, level, (T*)X, e0, e1);
     }
     return cudaErrorInvalidValue;
+}
+
+// the raw block X0 alone (one launch of k_init; its statistics go to scratch)
+template <typename T, int K>
+static cudaError_t run_test_vectors(gr_ctx* c, uint64_t seed, int level, T* X) {
+    cudaStream_t s = c->stream;
+    const int64_t n = c->n;
+    constexpr int GP = RowLayout<T, K>::GP;
+    void *p_st, *p_part;
+    GR_CUDA(c->ws.get(WS_SMOOTH_STATS, sizeof(double) * 4 * K + 64, &p_st));
+    double* st0 = (double*)p_st;
+    unsigned* counter = (unsigned*)(st0 + 4 * K);
+    const int init_rows = SM_WARPS * (32 / GP);
+    const int64_t iwant = ceil_div(n, init_rows);
+    const int64_t cap = (int64_t)c->num_sms * 8;
+    const int igrid = (int)(iwant < cap ? (iwant > 0 ? iwant : 1) : cap);
+    GR_CUDA(c->ws.get(WS_SMOOTH_PART, sizeof(double) * 2 * K * (size_t)(igrid > cap ? igrid : cap), &p_part));
+    GR_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned), s));
+    k_init<T, K><<<igrid, SM_THREADS, 0, s>>>(n, seed, (uint64_t)level, X, (double*)p_part, counter, st0);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t test_vectors_typed(gr_ctx* c, int K, uint64_t seed, int level, void* X) {
+    switch (K) {
+        case 4: return run_test_vectors<T, 4>(c, seed, level, (T*)X);
+        case 8: return run_test_vectors<T, 8>(c, seed, level, (T*)X);
+        case 16: return run_test_vectors<T, 16>(c, seed, level, (T*)X);
+        case 24: return run_test_vectors<T, 24>(c, seed, level, (T*)X);
+        case 32: return run_test_vectors<T, 32>(c, seed, level, (T*)X);
+    }
+    return cudaErrorInvalidValue;
+}
+
+gr_status test_vectors_impl(gr_ctx* c, int K, uint64_t seed, int level, gr_prec prec, void* X) {
+    cudaError_t e;
+    switch (prec) {
+        case GR_F64: e = test_vectors_typed<double>(c, K, seed, level, X); break;
+        case GR_F32: e = test_vectors_typed<float>(c, K, seed, level, X); break;
+        case GR_BF16: e = test_vectors_typed<__nv_bfloat16>(c, K, seed, level, X); break;
+        default: return set_error(c, GR_EINVAL, "test_vectors: unknown precision");
+    }
+    if (e != cudaSuccess) return cuda_error(c, e, "test_vectors");
+    return GR_OK;
 }
 
 gr_status smooth_impl(gr_ctx* c, int K, int sweeps, double omega, uint64_t seed, int level,
