@@ -364,6 +364,89 @@ __global__ void k_pairs_keys(int32_t npairs, const uint64_t* __restrict__ phi,
     idx[i] = (uint32_t)i;
 }
 
+// Truncation without a sort: keep[i] = 1 for the `allowed` smallest of the
+// npairs unique keys (hi, lo), ordered lexicographically, 0 for the others.
+// One block finds the key of rank allowed - 1 by radix selection, 8-bit
+// digits from the top (8 passes over hi, then 4 over lo when lo is part of
+// the key), then marks every key at or below it.
+constexpr int SELECT_THREADS = 1024;
+constexpr int32_t SELECT_MAX = 65536;  // larger sets take the radix sort
+
+template <bool D64>
+__global__ void __launch_bounds__(SELECT_THREADS) k_select_smallest(int32_t npairs, int32_t allowed,
+                                                                     const uint64_t* __restrict__ phi,
+                                                                     const uint32_t* __restrict__ plo,
+                                                                     int32_t* __restrict__ keep) {
+    __shared__ uint32_t hist[256];
+    __shared__ uint64_t pre_hi;
+    __shared__ uint32_t pre_lo;
+    __shared__ int32_t rank;
+    constexpr int NPASS = D64 ? 12 : 8;
+    if (threadIdx.x == 0) {
+        pre_hi = 0ull;
+        pre_lo = 0u;
+        rank = allowed - 1;
+    }
+    for (int pass = 0; pass < NPASS; ++pass) {
+        for (int t = threadIdx.x; t < 256; t += blockDim.x) hist[t] = 0u;
+        __syncthreads();
+        const bool in_hi = pass < 8;
+        const int sh = in_hi ? 56 - 8 * pass : 24 - 8 * (pass - 8);
+        const uint64_t mhi = in_hi ? (pass == 0 ? 0ull : ~0ull << (64 - 8 * pass)) : ~0ull;
+        const uint32_t mlo = in_hi || pass == 8 ? 0u : ~0u << (32 - 8 * (pass - 8));
+        const uint64_t ph = pre_hi;
+        const uint32_t pl = pre_lo;
+        for (int32_t i = threadIdx.x; i < npairs; i += blockDim.x) {
+            const uint64_t h = phi[i];
+            const uint32_t l = D64 ? plo[i] : 0u;
+            if ((h & mhi) == (ph & mhi) && (l & mlo) == (pl & mlo)) {
+                const uint32_t dig = in_hi ? (uint32_t)(h >> sh) & 255u : (l >> sh) & 255u;
+                atomicAdd(&hist[dig], 1u);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            const int lane = threadIdx.x;
+            uint32_t c[8], sum = 0u;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                c[j] = hist[lane * 8 + j];
+                sum += c[j];
+            }
+            uint32_t incl = sum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t x = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += x;
+            }
+            const uint32_t excl = incl - sum, r = (uint32_t)rank;
+            if (excl <= r && r < incl) {  // exactly one lane: rank < number of matching keys
+                uint32_t below = excl;
+                int b = lane * 8;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    if (r < below + c[j]) {
+                        b = lane * 8 + j;
+                        break;
+                    }
+                    below += c[j];
+                }
+                if (in_hi) pre_hi = ph | ((uint64_t)b << sh);
+                else pre_lo = pl | ((uint32_t)b << sh);
+                rank = (int32_t)(r - below);
+            }
+        }
+        __syncthreads();
+    }
+    const uint64_t kh = pre_hi;
+    const uint32_t kl = pre_lo;
+    for (int32_t i = threadIdx.x; i < npairs; i += blockDim.x) {
+        const uint64_t h = phi[i];
+        const bool le = D64 ? (h < kh || (h == kh && plo[i] <= kl)) : h <= kh;
+        keep[i] = le ? 1 : 0;
+    }
+}
+
 __global__ void k_keep_first(int32_t npairs, int64_t allowed, const uint32_t* __restrict__ sorted_idx,
                              int32_t* __restrict__ keep) {
     int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -549,7 +632,16 @@ gr_status aggregate_impl(gr_ctx* c, const void* d, int d_is_f64, int64_t target_
         const int32_t npairs = hctr[1];
         if (npairs == 0 || allowed <= 0) break;
         const unsigned gp = (unsigned)ceil_div(npairs, 256);
-        if ((int64_t)npairs > allowed) {
+        if ((int64_t)npairs > allowed && npairs <= SELECT_MAX) {
+            // keep the `allowed` smallest keys: one block selects them
+            if (d_is_f64) {
+                k_select_smallest<true><<<1, SELECT_THREADS, 0, s>>>(npairs, (int32_t)allowed, S.phi, S.plo, S.keep);
+            } else {
+                k_select_smallest<false><<<1, SELECT_THREADS, 0, s>>>(npairs, (int32_t)allowed, S.phi, S.plo, S.keep);
+            }
+            count_launch();
+            n_cur -= allowed;
+        } else if ((int64_t)npairs > allowed) {
             // keep the `allowed` smallest keys: stable sort by lo, then by hi
             void* pk;
             GR_TRY_CUDA(c, c->ws.get(WS_AGG_KEYS, (size_t)npairs * 32 + 1024, &pk), "scratch");

@@ -258,6 +258,23 @@ def test_aggregate_bitexact_oracle_d(gr, oracle_mod, case):
     assert nc32 == rnc32 and np.array_equal(agg32.cpu().numpy(), ref32)
 
 
+@pytest.mark.parametrize("n, drop", [(60000, 9000), (200000, 50000)])
+def test_aggregate_truncation_select_and_sort(gr, oracle_mod, n, drop):
+    # one pass with a target below what the matching reaches, so only the
+    # `allowed` smallest pairs merge: one block selects them up to 65,536
+    # pairs, the radix sort above that; 50 distinct distances, so edge ids
+    # break most ties
+    g = W.random_sparse(n, 4 * n, seed=n)
+    d = np.random.default_rng(n).integers(0, 50, g.m).astype(np.float64) / 50.0
+    target = n - drop
+    G = gr.graph_reduce_create(g.n, g.u, g.v, g.w)
+    for dd in (d, d.astype(np.float32)):
+        ref, rnc = oracle_mod.aggregate(g.n, g.u, g.v, dd.astype(np.float64), target, 1)
+        agg, nc, _ = gr.graph_reduce_aggregate(G, torch.from_numpy(dd).to(DEV), target, 1)
+        assert nc == rnc == target
+        assert np.array_equal(agg.cpu().numpy(), ref)
+
+
 def test_aggregate_ties_and_errors(gr, oracle_mod):
     g = W.grid2d(30, 30)
     d = np.round(np.random.default_rng(1).uniform(size=g.m), 1)  # heavy ties -> edge id decides
