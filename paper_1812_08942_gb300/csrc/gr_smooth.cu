@@ -146,14 +146,17 @@ __device__ __forceinline__ double scaled_int_to_f64(int64_t t) {
 // even rounding of t whenever that grid lies two bits below t's last kept
 // bit, i.e. |t| >= 2^30; smaller |t| fit in 32 bits and take the 32-bit
 // conversion, which rounds to nearest even itself.
-__device__ __forceinline__ float scaled_int_to_f32(int64_t t) {
-    const int32_t hi = (int32_t)(t >> 29);
+// hi = t >> 29 = (z >> 40) - 2^23 and lo = bits 11..39 of z come straight
+// from the generator output's two 32-bit halves.
+__device__ __forceinline__ float uniform_pm1_f32(uint64_t z) {
+    const uint32_t zh = (uint32_t)(z >> 32), zl = (uint32_t)z;
+    const int32_t hi = (int32_t)(zh >> 8) - (1 << 23);
+    const uint32_t lo = __funnelshift_r(zl, zh, 11) & 0x1fffffffu;
     if ((uint32_t)(hi + 2) > 3u) {  // hi >= 2 or hi <= -3: |t| >= 2^30
-        const uint32_t lo = (uint32_t)t & 0x1fffffffu;
         const uint32_t lo_odd = (lo & ~31u) | ((lo & 31u) ? 32u : 0u);
         return (__int2float_rn(hi) * 0x1p29f + __uint2float_rn(lo_odd)) * 0x1p-52f;
     }
-    return __int2float_rn((int32_t)t) * 0x1p-52f;
+    return __int2float_rn((int32_t)((uint32_t)hi << 29) + (int32_t)lo) * 0x1p-52f;  // |t| < 2^30
 }
 
 template <typename T>
@@ -164,7 +167,7 @@ __device__ __forceinline__ double uniform_pm1<double>(uint64_t z) {
 }
 template <>
 __device__ __forceinline__ float uniform_pm1<float>(uint64_t z) {
-    return scaled_int_to_f32(uniform_pm1_int(z));
+    return uniform_pm1_f32(z);
 }
 template <>
 __device__ __forceinline__ float uniform_pm1<__nv_bfloat16>(uint64_t z) {
@@ -208,6 +211,22 @@ __global__ void __launch_bounds__(SM_THREADS) k_init(int64_t n, uint64_t seed, u
         }
     }
     block_stats<Acc, K, E, G, GP>(s1, s2, part, counter, n, stats_out);
+}
+
+// k_init's grid: one full wave of resident blocks (a larger grid would leave
+// a ragged second wave), fewer when there are few rows
+template <typename T, int K>
+static int init_grid(const gr_ctx* c, int64_t n) {
+    static int occ = 0;
+    if (!occ) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_init<T, K>, SM_THREADS, 0) != cudaSuccess || occ < 1)
+            occ = 1;
+        if (occ > 8) occ = 8;
+    }
+    constexpr int GP = RowLayout<T, K>::GP;
+    const int64_t want = ceil_div(n, (int64_t)SM_WARPS * (32 / GP));
+    const int64_t cap = (int64_t)c->num_sms * occ;
+    return (int)(want < cap ? (want > 0 ? want : 1) : cap);
 }
 
 // ---------------------------------------------------------------------------
@@ -739,13 +758,18 @@ static cudaError_t launch_sweep_stream_lpr(gr_ctx* c, const T* Ain, T* Aout, dou
 template <typename T, int K>
 static cudaError_t launch_sweep_row(gr_ctx* c, const T* Ain, T* Aout, double omega, const double* st_in,
                                     double* part, int part_cap, unsigned* counter, double* st_out) {
-    constexpr int U = 2;
-    static int bps = 0;
-    if (!bps) {
-        GR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_sweep_row<T, K, U>, SM_THREADS, 0));
-        if (bps < 1) bps = 1;
+    // two slots in flight per lane; four on rows of mean degree >= 10 in
+    // FP32/BF16 storage (measured: 13-19 % faster there, slower in FP64 and
+    // on shorter rows).  The products are added in slot order either way.
+    static int bps2 = 0, bps4 = 0;
+    if (!bps2) {
+        GR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps2, k_sweep_row<T, K, 2>, SM_THREADS, 0));
+        GR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps4, k_sweep_row<T, K, 4>, SM_THREADS, 0));
+        if (bps2 < 1) bps2 = 1;
+        if (bps4 < 1) bps4 = 1;
     }
-    int grid = c->num_sms * bps;
+    const bool four = sizeof(T) < 8 && c->n > 0 && 2.0 * (double)c->m / (double)c->n >= 10.0;
+    int grid = c->num_sms * (four ? bps4 : bps2);
     if (grid > part_cap) grid = part_cap;
     const typename SlotOf<T>::type* slots;
     if constexpr (sizeof(T) == 8) {
@@ -760,8 +784,12 @@ static cudaError_t launch_sweep_row(gr_ctx* c, const T* Ain, T* Aout, double ome
     } else {
         slots = c->cw32;
     }
-    k_sweep_row<T, K, U><<<grid, SM_THREADS, 0, c->stream>>>(c->n, c->rowptr, slots, Ain, Aout, omega, st_in, part,
-                                                             counter, st_out);
+    if (four)
+        k_sweep_row<T, K, 4><<<grid, SM_THREADS, 0, c->stream>>>(c->n, c->rowptr, slots, Ain, Aout, omega, st_in, part,
+                                                                 counter, st_out);
+    else
+        k_sweep_row<T, K, 2><<<grid, SM_THREADS, 0, c->stream>>>(c->n, c->rowptr, slots, Ain, Aout, omega, st_in, part,
+                                                                 counter, st_out);
     count_launch();
     return cudaGetLastError();
 }
@@ -803,9 +831,7 @@ static cudaError_t run_smooth(gr_ctx* c, int sweeps, double omega, uint64_t seed
     const int64_t want = ceil_div(n, rows_per_block);
     const int64_t cap = (int64_t)c->num_sms * 8;
     const int grid = (int)(want < cap ? (want > 0 ? want : 1) : cap);
-    const int init_rows = SM_WARPS * (32 / GP);
-    const int64_t iwant = ceil_div(n, init_rows);
-    const int igrid = (int)(iwant < cap ? (iwant > 0 ? iwant : 1) : cap);
+    const int igrid = init_grid<T, K>(c, n);
     // the streaming sweep runs a persistent grid of at most 8 blocks per SM
     int maxgrid = grid > igrid ? grid : igrid;
     if (c->num_sms * 8 > maxgrid) maxgrid = c->num_sms * 8;
@@ -861,11 +887,9 @@ static cudaError_t run_test_vectors(gr_ctx* c, uint64_t seed, int level, T* X) {
     GR_CUDA(c->ws.get(WS_SMOOTH_STATS, sizeof(double) * 4 * K + 64, &p_st));
     double* st0 = (double*)p_st;
     unsigned* counter = (unsigned*)(st0 + 4 * K);
-    const int init_rows = SM_WARPS * (32 / GP);
-    const int64_t iwant = ceil_div(n, init_rows);
     const int64_t cap = (int64_t)c->num_sms * 8;
-    const int igrid = (int)(iwant < cap ? (iwant > 0 ? iwant : 1) : cap);
-    GR_CUDA(c->ws.get(WS_SMOOTH_PART, sizeof(double) * 2 * K * (size_t)(igrid > cap ? igrid : cap), &p_part));
+    const int igrid = init_grid<T, K>(c, n);
+    GR_CUDA(c->ws.get(WS_SMOOTH_PART, sizeof(double) * 2 * K * (size_t)cap, &p_part));
     GR_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned), s));
     k_init<T, K><<<igrid, SM_THREADS, 0, s>>>(n, seed, (uint64_t)level, X, (double*)p_part, counter, st0);
     count_launch();
@@ -1150,10 +1174,7 @@ static gr_status run_smooth_gs(gr_ctx* c, int sweeps, double omega, uint64_t see
     GR_TRY_CUDA(c, c->ws.get(WS_SMOOTH_STATS, sizeof(double) * 4 * K + 64, &p_st), "scratch");
     double* st = (double*)p_st;
     unsigned* counter = (unsigned*)(st + 4 * K);
-    const int init_rows = SM_WARPS * (32 / GP);
-    const int64_t cap = (int64_t)c->num_sms * 8;
-    const int64_t iwant = ceil_div(n, init_rows);
-    const int igrid = (int)(iwant < cap ? (iwant > 0 ? iwant : 1) : cap);
+    const int igrid = init_grid<T, K>(c, n);
     GR_TRY_CUDA(c, c->ws.get(WS_SMOOTH_PART, sizeof(double) * 2 * K * (size_t)igrid, &p_part), "scratch");
     double* part = (double*)p_part;
     GR_TRY_CUDA(c, cudaMemsetAsync(counter, 0, sizeof(unsigned), s), "memset");
@@ -1278,8 +1299,7 @@ static gr_status run_smooth_noalloc(gr_ctx* c, int sweeps, double omega, uint64_
     const int64_t cap = (int64_t)c->num_sms * 8;
     const int64_t want = ceil_div(n, rows_per_block);
     const int grid = (int)(want < cap ? (want > 0 ? want : 1) : cap);
-    const int64_t iwant = ceil_div(n, SM_WARPS * (32 / GP));
-    const int igrid = (int)(iwant < cap ? (iwant > 0 ? iwant : 1) : cap);
+    const int igrid = init_grid<T, K>(c, n);
     const int maxgrid = grid > igrid ? grid : igrid;
     // layout of the shared scratch: [vector block | 2 x 2K stats + counter | partials]
     const size_t b_buf = align256(sizeof(T) * (size_t)n * K);
