@@ -351,7 +351,7 @@ gr_status galerkin_rows(gr_ctx* c, const int32_t* agg, int64_t nc, gr_ctx* cc, b
     const int32_t nmed = hc[1];
     const unsigned long long smax = ((const unsigned long long*)hs)[2];
     // (the register path packs B into 27 bits)
-    if (smax > (unsigned long long)MEDIUM_P || (int64_t)nmed * 16 > nc || nc >= (int64_t(1) << 27)) {
+    if (smax > (unsigned long long)MEDIUM_P || nc >= (int64_t(1) << 27)) {
         *too_long = true;
         return GR_OK;
     }
