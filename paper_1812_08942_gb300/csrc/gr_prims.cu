@@ -204,6 +204,7 @@ constexpr int SORT_THREADS = 256;
 constexpr int SORT_WARPS = SORT_THREADS / 32;
 constexpr int SORT_CHUNKS = 8;  // chunks of 32 keys per warp
 constexpr int SORT_TILE = SORT_THREADS * SORT_CHUNKS;
+static_assert(SORT_THREADS == RADIX, "the scatter handles one digit per thread");
 
 template <typename KT>
 __global__ void __launch_bounds__(SORT_THREADS) k_radix_hist(const KT* __restrict__ keys,
@@ -222,21 +223,32 @@ __global__ void __launch_bounds__(SORT_THREADS) k_radix_hist(const KT* __restric
     for (int d = threadIdx.x; d < RADIX; d += SORT_THREADS) hist[(int64_t)d * nb + blockIdx.x] = cnt[d];
 }
 
+// Stable scatter of one tile.  Every warp ranks its 8 chunks of 32 keys per
+// digit with __match_any_sync (warp order = input order); the block then
+// places its keys in shared memory in (digit, input) order and writes them
+// out sequentially, so consecutive threads store consecutive addresses of a
+// digit's output run instead of scattering one key per lane.
 template <typename KT>
 __global__ void __launch_bounds__(SORT_THREADS) k_radix_scatter(
     const KT* __restrict__ keys, const uint32_t* __restrict__ vals, int64_t count, int shift,
     const int32_t* __restrict__ offs, int nb, KT* __restrict__ keys_out,
     uint32_t* __restrict__ vals_out) {
-    __shared__ int32_t whist[SORT_WARPS][RADIX];
+    __shared__ int32_t whist[SORT_WARPS][RADIX];  // counts, then smem bases per (warp, digit)
+    __shared__ int32_t tstart[RADIX];            // tile-local start of each digit
+    __shared__ int32_t gbase[RADIX];             // global start of this tile's run of each digit
+    __shared__ int32_t wsum[SORT_WARPS];
+    __shared__ KT skey[SORT_TILE];
+    __shared__ uint32_t sval[SORT_TILE];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
-    const int64_t wbase = (int64_t)blockIdx.x * SORT_TILE + (int64_t)warp * 32 * SORT_CHUNKS;
+    const int64_t tbase = (int64_t)blockIdx.x * SORT_TILE;
+    const int64_t wbase = tbase + (int64_t)warp * 32 * SORT_CHUNKS;
     KT k[SORT_CHUNKS];
     uint32_t v[SORT_CHUNKS];
-    int dig[SORT_CHUNKS];
+    int dig[SORT_CHUNKS], rnk[SORT_CHUNKS];
 #pragma unroll
     for (int c = 0; c < SORT_CHUNKS; ++c) {
-        int64_t idx = wbase + c * 32 + lane;
+        const int64_t idx = wbase + c * 32 + lane;
         if (idx < count) {
             k[c] = keys[idx];
             v[c] = vals[idx];
@@ -249,36 +261,60 @@ __global__ void __launch_bounds__(SORT_THREADS) k_radix_scatter(
     }
     for (int d = lane; d < RADIX; d += 32) whist[warp][d] = 0;
     __syncwarp();
+    // rank of every key among the warp's keys of its digit
 #pragma unroll
     for (int c = 0; c < SORT_CHUNKS; ++c) {
-        unsigned peers = __match_any_sync(0xffffffffu, dig[c]);
-        int leader = __ffs(peers) - 1;
-        if (lane == leader && dig[c] < RADIX) whist[warp][dig[c]] += __popc(peers);
+        const unsigned peers = __match_any_sync(0xffffffffu, dig[c]);
+        const int leader = __ffs(peers) - 1;
+        const int before = dig[c] < RADIX ? whist[warp][dig[c]] : 0;
+        rnk[c] = before + __popc(peers & lt_mask);
+        __syncwarp();
+        if (lane == leader && dig[c] < RADIX) whist[warp][dig[c]] = before + __popc(peers);
         __syncwarp();
     }
     __syncthreads();
-    // per digit: base of every warp = global tile offset + counts of earlier warps
-    for (int d = threadIdx.x; d < RADIX; d += SORT_THREADS) {
-        int32_t run = offs[(int64_t)d * nb + blockIdx.x];
-        for (int w = 0; w < SORT_WARPS; ++w) {
-            int32_t c = whist[w][d];
-            whist[w][d] = run;
-            run += c;
-        }
+    // per digit (one thread each): the tile's count, the warps' bases within
+    // the digit, and the digit's global start
+    const int d = threadIdx.x;  // SORT_THREADS == RADIX
+    int32_t tot = 0;
+    for (int w = 0; w < SORT_WARPS; ++w) {
+        const int32_t c = whist[w][d];
+        whist[w][d] = tot;
+        tot += c;
     }
+    gbase[d] = offs[(int64_t)d * nb + blockIdx.x];
+    // exclusive scan of the digit totals over the block
+    int32_t incl = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t x = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += x;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    int32_t wpre = 0;
+    for (int w = 0; w < warp; ++w) wpre += wsum[w];
+    const int32_t start = wpre + incl - tot;
+    tstart[d] = start;
+    for (int w = 0; w < SORT_WARPS; ++w) whist[w][d] += start;
     __syncthreads();
 #pragma unroll
     for (int c = 0; c < SORT_CHUNKS; ++c) {
-        unsigned peers = __match_any_sync(0xffffffffu, dig[c]);
-        int leader = __ffs(peers) - 1;
         if (dig[c] < RADIX) {
-            int32_t pos = whist[warp][dig[c]] + __popc(peers & lt_mask);
-            keys_out[pos] = k[c];
-            vals_out[pos] = v[c];
+            const int32_t pos = whist[warp][dig[c]] + rnk[c];
+            skey[pos] = k[c];
+            sval[pos] = v[c];
         }
-        __syncwarp();
-        if (lane == leader && dig[c] < RADIX) whist[warp][dig[c]] += __popc(peers);
-        __syncwarp();
+    }
+    __syncthreads();
+    int32_t total = 0;
+    for (int w = 0; w < SORT_WARPS; ++w) total += wsum[w];
+    for (int j = threadIdx.x; j < total; j += SORT_THREADS) {
+        const KT key = skey[j];
+        const int dj = (int)((key >> shift) & (RADIX - 1));
+        const int32_t g = gbase[dj] + (j - tstart[dj]);
+        keys_out[g] = key;
+        vals_out[g] = sval[j];
     }
 }
 
