@@ -307,18 +307,40 @@ __global__ void __launch_bounds__(256) k_suitor(
     if ((threadIdx.x & 31) == 0 && mine) atomicAdd(proposals, mine);
 }
 
-// start of a pass: clear the suitor keys; from the second pass on, list the heads
+// start of a pass: clear the suitor keys; from the second pass on, list the
+// heads (one atomic per block on the list length: about half the nodes are
+// heads, and one per warp serialised on the counter)
+constexpr int INIT_THREADS = 256;
+
 template <bool D64>
-__global__ void k_suitor_init(int64_t n, const int32_t* __restrict__ cl, void* ws, int32_t* __restrict__ wl,
-                              int32_t* __restrict__ count, int list_heads) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    if constexpr (D64) ((int32_t*)ws)[i] = -1;
-    else ((unsigned long long*)ws)[i] = ~0ull;
-    if (list_heads) {
-        const int32_t k = warp_slot(cl[i] == (int32_t)i, count);
-        if (k >= 0) wl[k] = (int32_t)i;
+__global__ void __launch_bounds__(INIT_THREADS) k_suitor_init(int64_t n, const int32_t* __restrict__ cl, void* ws,
+                                                              int32_t* __restrict__ wl, int32_t* __restrict__ count,
+                                                              int list_heads) {
+    __shared__ int32_t wbase[INIT_THREADS / 32];
+    __shared__ int32_t bbase;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool in = i < n;
+    if (in) {
+        if constexpr (D64) ((int32_t*)ws)[i] = -1;
+        else ((unsigned long long*)ws)[i] = ~0ull;
     }
+    if (!list_heads) return;  // uniform over the grid
+    const bool head = in && cl[i] == (int32_t)i;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned bal = __ballot_sync(0xffffffffu, head);
+    if (lane == 0) wbase[warp] = __popc(bal);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int32_t tot = 0;
+        for (int w = 0; w < INIT_THREADS / 32; ++w) {
+            const int32_t c = wbase[w];
+            wbase[w] = tot;
+            tot += c;
+        }
+        bbase = tot > 0 ? atomicAdd(count, tot) : 0;
+    }
+    __syncthreads();
+    if (head) wl[bbase + wbase[warp] + __popc(bal & ((1u << lane) - 1u))] = (int32_t)i;
 }
 
 // Matched pairs: b and its suitor a hold each other's key.  Any one-sided
@@ -594,8 +616,9 @@ gr_status aggregate_impl(gr_ctx* c, const void* d, int d_is_f64, int64_t target_
         if (!deferred && n_cur <= target_nc) break;
         const bool first = pass == 0;
         GR_TRY_CUDA(c, cudaMemsetAsync(S.ctr, 0, 16, s), "memset");
-        if (d_is_f64) k_suitor_init<true><<<gn, 256, 0, s>>>(n, S.cl, S.ws, S.wl, S.ctr + 0, first ? 0 : 1);
-        else k_suitor_init<false><<<gn, 256, 0, s>>>(n, S.cl, S.ws, S.wl, S.ctr + 0, first ? 0 : 1);
+        const unsigned gi = (unsigned)ceil_div(n > 0 ? n : 1, INIT_THREADS);
+        if (d_is_f64) k_suitor_init<true><<<gi, INIT_THREADS, 0, s>>>(n, S.cl, S.ws, S.wl, S.ctr + 0, first ? 0 : 1);
+        else k_suitor_init<false><<<gi, INIT_THREADS, 0, s>>>(n, S.cl, S.ws, S.wl, S.ctr + 0, first ? 0 : 1);
         count_launch();
         if (d_is_f64) launch_suitor_lpc<true>(c, S, lpc, n_cur, d, chain_cap, first);
         else launch_suitor_lpc<false>(c, S, lpc, n_cur, d, chain_cap, first);
