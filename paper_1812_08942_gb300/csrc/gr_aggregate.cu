@@ -316,8 +316,6 @@ template <bool D64>
 __global__ void __launch_bounds__(INIT_THREADS) k_suitor_init(int64_t n, const int32_t* __restrict__ cl, void* ws,
                                                               int32_t* __restrict__ wl, int32_t* __restrict__ count,
                                                               int list_heads) {
-    __shared__ int32_t wbase[INIT_THREADS / 32];
-    __shared__ int32_t bbase;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool in = i < n;
     if (in) {
@@ -326,27 +324,18 @@ __global__ void __launch_bounds__(INIT_THREADS) k_suitor_init(int64_t n, const i
     }
     if (!list_heads) return;  // uniform over the grid
     const bool head = in && cl[i] == (int32_t)i;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const unsigned bal = __ballot_sync(0xffffffffu, head);
-    if (lane == 0) wbase[warp] = __popc(bal);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int32_t tot = 0;
-        for (int w = 0; w < INIT_THREADS / 32; ++w) {
-            const int32_t c = wbase[w];
-            wbase[w] = tot;
-            tot += c;
-        }
-        bbase = tot > 0 ? atomicAdd(count, tot) : 0;
-    }
-    __syncthreads();
-    if (head) wl[bbase + wbase[warp] + __popc(bal & ((1u << lane) - 1u))] = (int32_t)i;
+    const int32_t k = block_slot<INIT_THREADS>(head, count);
+    if (k >= 0) wl[k] = (int32_t)i;
 }
 
 // Matched pairs: b and its suitor a hold each other's key.  Any one-sided
-// suitor left at termination is an internal error (flag).
+// suitor left at termination is an internal error (flag).  Every block runs
+// the same number of rounds, so the pair list grows by one atomic per block
+// and round.
+constexpr int PAIR_THREADS = 256;
+
 template <bool D64, bool FIRST_PASS>
-__global__ void k_suitor_pairs(const int32_t* __restrict__ wl, const int32_t* __restrict__ wl_count, int64_t n,
+__global__ void __launch_bounds__(PAIR_THREADS) k_suitor_pairs(const int32_t* __restrict__ wl, const int32_t* __restrict__ wl_count, int64_t n,
                                const void* ws, const void* __restrict__ d, const int32_t* __restrict__ eu,
                                const int32_t* __restrict__ ev, const int32_t* __restrict__ cl,
                                int32_t* __restrict__ pc, int32_t* __restrict__ pb, uint64_t* __restrict__ phi,
@@ -355,18 +344,22 @@ __global__ void k_suitor_pairs(const int32_t* __restrict__ wl, const int32_t* __
     using T = SK<D64>;
     const int64_t count = FIRST_PASS ? n : (int64_t)*wl_count;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
-        const int32_t b = FIRST_PASS ? (int32_t)i : wl[i];
-        const typename T::K k = T::load(ws, d, b);
-        int32_t a = -1;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x; r < count; r += stride) {
+        const int64_t i = r + threadIdx.x;
+        int32_t b = -1, a = -1;
+        typename T::K k{};
         bool emit = false;
-        if (!T::is_inf(k)) {
-            a = other_end<FIRST_PASS>(T::edge(k), b, eu, ev, cl);
-            const typename T::K ka = T::load(ws, d, a);
-            if (T::less(ka, k) || T::less(k, ka)) atomicExch(err_mutual, 1);
-            emit = b < a;
+        if (i < count) {
+            b = FIRST_PASS ? (int32_t)i : wl[i];
+            k = T::load(ws, d, b);
+            if (!T::is_inf(k)) {
+                a = other_end<FIRST_PASS>(T::edge(k), b, eu, ev, cl);
+                const typename T::K ka = T::load(ws, d, a);
+                if (T::less(ka, k) || T::less(k, ka)) atomicExch(err_mutual, 1);
+                emit = b < a;
+            }
         }
-        const int32_t s = warp_slot(emit, npairs);
+        const int32_t s = block_slot<PAIR_THREADS>(emit, npairs);
         if (s >= 0) {
             pc[s] = b;
             pb[s] = a;
@@ -535,7 +528,7 @@ static void launch_suitor(gr_ctx* c, AggState& S, int64_t count, const void* d, 
         (unsigned long long*)(S.ctr + 2), S.ctr + 5, S.ctr + 6);
     count_launch();
     const int64_t pwant = count > 0 ? ceil_div(count, 256) : 1, pcap = (int64_t)c->num_sms * 16;
-    k_suitor_pairs<D64, FIRST_PASS><<<(unsigned)(pwant < pcap ? pwant : pcap), 256, 0, c->stream>>>(
+    k_suitor_pairs<D64, FIRST_PASS><<<(unsigned)(pwant < pcap ? pwant : pcap), PAIR_THREADS, 0, c->stream>>>(
         S.wl, S.ctr + 0, c->n, S.ws, d, c->eu, c->ev, S.cl, S.pc, S.pb, S.phi, S.plo, S.ctr + 1, S.ctr + 7);
     count_launch();
 }

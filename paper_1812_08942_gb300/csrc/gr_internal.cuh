@@ -123,6 +123,32 @@ cudaError_t degree_scale(gr_ctx* c);
 // for per-row sorting, sets *too_long and leaves cc untouched.
 gr_status galerkin_rows(gr_ctx* c, const int32_t* agg, int64_t nc, gr_ctx* cc, bool* too_long);
 
+// Slot of the calling thread in a list that grows by one entry per thread
+// with `keep` set: one atomic per block, entries in thread order within the
+// block; -1 if !keep.  Every thread of the block must call it (it holds
+// barriers); BT is the block size.
+template <int BT>
+__device__ __forceinline__ int32_t block_slot(bool keep, int32_t* count) {
+    __shared__ int32_t wbase[BT / 32];
+    __shared__ int32_t bbase;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+    __syncthreads();  // the previous call's readers are done
+    if (lane == 0) wbase[warp] = __popc(bal);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int32_t tot = 0;
+        for (int w = 0; w < BT / 32; ++w) {
+            const int32_t c = wbase[w];
+            wbase[w] = tot;
+            tot += c;
+        }
+        bbase = tot > 0 ? atomicAdd(count, tot) : 0;
+    }
+    __syncthreads();
+    return keep ? bbase + wbase[warp] + __popc(bal & ((1u << lane) - 1u)) : -1;
+}
+
 // Slot of the calling lane in a list that grows by one entry per lane with
 // `keep` set: one atomic per warp, entries in lane order; -1 if !keep.
 __device__ __forceinline__ int32_t warp_slot(bool keep, int32_t* count) {
