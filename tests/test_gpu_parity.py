@@ -331,14 +331,14 @@ def _tier_labels(n, sizes, seed):
 
 
 # Coarse rows of up to 128 slots are assembled by the small-row kernel, up to
-# 1,024 by the medium one; longer rows (or many medium ones) send the whole
-# product to the global sort.  Aggregates of 1-3, 40, 600 and 3,000 members of
-# a graph of mean degree ~10 reach each path.
+# 1,024 by the medium one; a longer row sends the whole product to the global
+# sort.  Aggregates of 1-3, 40, 600 and 3,000 members of a graph of mean degree
+# ~10 reach each path.
 TIER_CASES = [
     ("all_medium", [40] * 150),
     ("small_and_medium", [1] * 3000 + [3] * 900 + [40] * 7),
     ("global_sort_long", [600] * 10),
-    ("global_sort_many_medium", [3000, 3000]),
+    ("global_sort_two_long", [3000, 3000]),
     ("mixed", [1] * 500 + [3] * 300 + [40] * 60 + [600] * 4 + [2000]),
 ]
 
@@ -361,6 +361,38 @@ def test_coarsen_row_tiers(gr, oracle_mod, case):
     X = torch.empty(nc, K, dtype=torch.float64, device=DEV)
     gr.graph_reduce_smooth(C, X, S, 0.7, 5, 1)
     assert _col_relerr(X.cpu().numpy(), ref).max() <= 1e-12
+
+
+def test_degenerate_graphs(gr, oracle_mod):
+    e, ew = np.zeros(0, np.int32), np.zeros(0)
+    # edgeless graphs: nothing merges, the identity map's coarse graph has no
+    # edge, and the level loop makes no level
+    for n in (7, 1):
+        G = gr.graph_reduce_create(n, e, e, ew)
+        agg, nc, _ = gr.graph_reduce_aggregate(G, torch.zeros(0, dtype=torch.float64, device=DEV), 1, 2)
+        ref, rnc = oracle_mod.aggregate(n, e, e, ew, 1, 2)
+        assert nc == rnc == n and np.array_equal(agg.cpu().numpy(), ref)
+        C = gr.graph_reduce_coarsen(G, agg, nc)
+        assert C.n == n and C.m == 0
+        levels, _ = gr.graph_reduce_multilevel(G, gr.ReduceParams(K=4, sweeps=3, prec=gr.GR_F64, final_target=1))
+        assert len(levels) == len(oracle_mod.reduce_multilevel(n, e, e, ew, 4, 3, final_target=1)) == 0
+    # one edge: one merge, a coarse graph of one node and no edge
+    u, v, w = np.array([0], np.int32), np.array([1], np.int32), np.array([2.5])
+    G = gr.graph_reduce_create(2, u, v, w)
+    agg, nc, _ = gr.graph_reduce_aggregate(G, torch.tensor([0.3], dtype=torch.float64, device=DEV), 1, 2)
+    assert nc == 1 and agg.cpu().tolist() == [0, 0]
+    C = gr.graph_reduce_coarsen(G, agg, 1)
+    assert C.n == 1 and C.m == 0
+    levels, _ = gr.graph_reduce_multilevel(G, gr.ReduceParams(K=4, sweeps=3, prec=gr.GR_F64, final_target=1))
+    ref = oracle_mod.reduce_multilevel(2, u, v, w, 4, 3, final_target=1)
+    assert len(levels) == len(ref) == 1 and levels[0].n == 1 and levels[0].m == 0
+    assert np.array_equal(gr.graph_reduce_get_map(levels[0]).cpu().numpy(), ref[0].agg)
+    # identity map: the coarse graph is the fine graph, weights bit for bit
+    g = W.random_sparse(1537, 6000, seed=4)
+    G = gr.graph_reduce_create(g.n, g.u, g.v, g.w)
+    C = gr.graph_reduce_coarsen(G, torch.arange(g.n, dtype=torch.int32, device=DEV), g.n)
+    cu, cv, cw = (t.numpy() for t in gr.graph_reduce_get_edges(C, on_host=True))
+    assert np.array_equal(cu, g.u) and np.array_equal(cv, g.v) and np.array_equal(cw, g.w)
 
 
 def test_coarsen_rejects_bad_labels(gr):
