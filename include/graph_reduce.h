@@ -100,14 +100,18 @@ gr_status graph_reduce_test_vectors(gr_ctx* ctx, int K, uint64_t seed, int level
  * allocate device memory once they are running: for example code working
  * inside a fixed, pre-reserved memory budget, or under another framework's
  * allocator, where a cudaMalloc / cudaMallocAsync from a library would break
- * the budget or the allocator's bookkeeping.  The paper has no counterpart;
- * the result is the same as graph_reduce_smooth's (same kernels, same order).
+ * the budget or the allocator's bookkeeping.  The paper has no counterpart.
+ * It runs graph_reduce_smooth's own launch sequence (same kernels, grids and
+ * order of additions), so X is bit for bit the same as graph_reduce_smooth's.
  * The caller passes the graph (ctx, created beforehand) and the output X, as
  * for graph_reduce_smooth.  The scratch -- the second n x K block, the column
- * statistics and per-block partial sums -- lives in one 32 MiB device array
+ * statistics and per-block partial sums, and, when the context does not hold
+ * them yet, the packed FP64 slots (16 bytes per CSR slot, FP64 blocks) and
+ * the streaming kernel's row partition -- lives in one 32 MiB device array
  * inside the library, held by every GPU that loads it until the process
- * exits; n*K*sizeof(element) plus about 1 MiB of statistics must fit, else
- * GR_EINVAL.  The first call on a device looks up that array's device address
+ * exits; what a call needs must fit, else GR_EINVAL (n*K*sizeof(element) plus
+ * about 1 MiB of statistics, and the rest as said).  Nothing is cached from
+ * the array into the context.  The first call on a device looks up that array's device address
  * (cudaGetSymbolAddress) and should come before any stream capture.  All
  * calls share the array and it keeps the last call's contents: calls that
  * overlap on the GPU (other streams, other contexts) race and corrupt each
@@ -115,6 +119,27 @@ gr_status graph_reduce_test_vectors(gr_ctx* ctx, int K, uint64_t seed, int level
  * routine is called. */
 gr_status graph_reduce_smooth_noalloc(gr_ctx* ctx, int K, int sweeps, double omega,
                                       uint64_t seed, int level, gr_prec prec, void* X);
+
+/* Sweep kernel behind graph_reduce_smooth and graph_reduce_smooth_noalloc on
+ * this context.  The paper has no counterpart: these are two implementations
+ * of the same weighted-Jacobi sweep (Alg. 3), each adding a row's products in
+ * slot order, so they agree within the rounding of the column statistics.
+ *   GR_SWEEP_AUTO    (default) the streaming kernel when rows are long (a
+ *                    warp's group of 32 / lanes-per-row rows would hold over
+ *                    128 slots), else the row-group kernel
+ *   GR_SWEEP_ROW     row-group kernel: one lane per 16-byte chunk of a vector
+ *                    row, several rows per warp, rows grid-strided
+ *   GR_SWEEP_STREAM  warp per row over a slot-balanced row partition, the
+ *                    slots staged through shared memory
+ * GR_EINVAL for any other value. */
+typedef enum { GR_SWEEP_AUTO = 0, GR_SWEEP_ROW = 1, GR_SWEEP_STREAM = 2 } gr_sweep_kernel;
+
+gr_status graph_reduce_set_sweep_kernel(gr_ctx* ctx, gr_sweep_kernel kind);
+
+/* The sweep kernel graph_reduce_smooth runs on this context for K and prec
+ * (no counterpart in the paper; for tuning and tests).
+ *   kernel_out   host: GR_SWEEP_ROW or GR_SWEEP_STREAM */
+gr_status graph_reduce_sweep_plan(gr_ctx* ctx, int K, gr_prec prec, int32_t* kernel_out);
 
 /* Test-vector smoothing with the Gauss-Seidel relaxation Sec. 3.2.1 names,
  * made parallel by a multicolour ordering.  The paper gives no ordering; this

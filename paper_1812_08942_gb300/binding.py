@@ -18,11 +18,12 @@ _lib = None
 
 GR_OK, GR_EINVAL, GR_ENOMEM, GR_ECUDA, GR_ETIMEOUT, GR_ESTATE = range(6)
 GR_F64, GR_F32, GR_BF16 = 0, 1, 2
+GR_SWEEP_AUTO, GR_SWEEP_ROW, GR_SWEEP_STREAM = range(3)
 _STATUS = {1: "GR_EINVAL", 2: "GR_ENOMEM", 3: "GR_ECUDA", 4: "GR_ETIMEOUT", 5: "GR_ESTATE"}
 
 EXPORTED = [
     "graph_reduce_create", "graph_reduce_get_info", "graph_reduce_test_vectors", "graph_reduce_smooth",
-    "graph_reduce_smooth_noalloc",
+    "graph_reduce_smooth_noalloc", "graph_reduce_set_sweep_kernel", "graph_reduce_sweep_plan",
     "graph_reduce_smooth_gs", "graph_reduce_colour",
     "graph_reduce_affinity",
     "graph_reduce_aggregate", "graph_reduce_coarsen", "graph_reduce_get_edges", "graph_reduce_get_map",
@@ -72,6 +73,8 @@ def load():
         "graph_reduce_test_vectors": (I, [P, I, U64, I, I, P]),
         "graph_reduce_smooth": (I, [P, I, I, D, U64, I, I, P]),
         "graph_reduce_smooth_noalloc": (I, [P, I, I, D, U64, I, I, P]),
+        "graph_reduce_set_sweep_kernel": (I, [P, I]),
+        "graph_reduce_sweep_plan": (I, [P, I, I, ctypes.POINTER(I32)]),
         "graph_reduce_smooth_gs": (I, [P, I, I, D, U64, I, U64, I, P]),
         "graph_reduce_colour": (I, [P, U64, P, ctypes.POINTER(I32)]),
         "graph_reduce_affinity": (I, [P, P, I, I, P, P]),
@@ -175,6 +178,18 @@ def graph_reduce_smooth(g: Graph, X, sweeps, omega=0.7, seed=0, level=0):
                                     _prec_of(X.dtype), _ptr(X))
     _check(st, g.handle)
     return X
+
+
+def graph_reduce_set_sweep_kernel(g: Graph, kind: int):
+    """Select the sweep kernel of g's smoothing calls (GR_SWEEP_*)."""
+    _check(load().graph_reduce_set_sweep_kernel(g.handle, int(kind)), g.handle)
+
+
+def graph_reduce_sweep_plan(g: Graph, K: int, dtype) -> int:
+    """The sweep kernel (GR_SWEEP_ROW / GR_SWEEP_STREAM) smoothing runs for K and dtype."""
+    kind = ctypes.c_int32()
+    _check(load().graph_reduce_sweep_plan(g.handle, int(K), _prec_of(dtype), ctypes.byref(kind)), g.handle)
+    return int(kind.value)
 
 
 def graph_reduce_test_vectors(g: Graph, X, seed=0, level=0):

@@ -116,6 +116,21 @@ gr_status graph_reduce_get_info(const gr_ctx* ctx, int64_t* n_out, int64_t* m_ou
     return GR_OK;
 }
 
+gr_status graph_reduce_set_sweep_kernel(gr_ctx* ctx, gr_sweep_kernel kind) {
+    if (!ctx) return set_error(nullptr, GR_EINVAL, "set_sweep_kernel: ctx is NULL");
+    if ((int)kind < (int)GR_SWEEP_AUTO || (int)kind > (int)GR_SWEEP_STREAM)
+        return set_error(ctx, GR_EINVAL, "set_sweep_kernel: unknown kernel");
+    ctx->sweep_kind = (int)kind;
+    return GR_OK;
+}
+
+gr_status graph_reduce_sweep_plan(gr_ctx* ctx, int K, gr_prec prec, int32_t* kernel_out) {
+    if (!ctx) return set_error(nullptr, GR_EINVAL, "sweep_plan: ctx is NULL");
+    if (!valid_K(K)) return set_error(ctx, GR_EINVAL, "sweep_plan: K must be 4, 8, 16, 24 or 32");
+    if (!kernel_out) return set_error(ctx, GR_EINVAL, "sweep_plan: kernel_out is NULL");
+    return sweep_plan_impl(ctx, K, prec, kernel_out);
+}
+
 gr_status graph_reduce_smooth(gr_ctx* ctx, int K, int sweeps, double omega, uint64_t seed, int level,
                               gr_prec prec, void* X) {
     if (!ctx) return set_error(nullptr, GR_EINVAL, "smooth: ctx is NULL");

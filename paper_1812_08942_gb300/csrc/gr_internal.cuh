@@ -73,6 +73,8 @@ struct gr_ctx {
     int32_t* wpart = nullptr;
     int64_t wpart_W = 0;
     int4* cw64 = nullptr;       // 2m: (col, 0, w / deg_row as FP64), built on first FP64 sweep
+    // sweep kernel selection (gr_sweep_kernel)
+    int sweep_kind = GR_SWEEP_AUTO;
     // multicolour Gauss-Seidel ordering for one colouring seed, built on first use:
     // nodes in ascending (colour, id) and each colour's range in that list
     int32_t* gs_order = nullptr;
@@ -188,6 +190,8 @@ gr_status loss_fwd_impl(gr_ctx* fine, gr_ctx* coarse, const int32_t* agg, const 
                         const float* w_c, int sweeps, double omega, float* loss, float* saved);
 gr_status loss_bwd_impl(gr_ctx* coarse, const float* saved, int K, const float* w_c, int sweeps,
                         double omega, const float* grad_loss, float* grad_w);
+
+gr_status sweep_plan_impl(gr_ctx* c, int K, gr_prec prec, int32_t* kind_out);
 
 gr_status set_error(gr_ctx* c, gr_status st, const std::string& msg);
 gr_status cuda_error(gr_ctx* c, cudaError_t e, const char* where);

@@ -10,6 +10,7 @@
 #include <cuda_bf16.h>
 
 #include "gr_internal.cuh"
+#include "gr_sweep.cuh"
 #include "gr_vec.cuh"
 
 namespace gr {
@@ -21,49 +22,6 @@ constexpr int SM_WARPS = SM_THREADS / 32;
 // Column statistics: per-block partial sums (FP64) and a last-block finish
 // that turns them into (mu, 1/s) for every column, in fixed order.
 // ---------------------------------------------------------------------------
-template <int K>
-__device__ void finish_stats(const double* __restrict__ part, int nblocks, int64_t n,
-                             double* __restrict__ stats_out) {
-    // 2K sums, each split over SM_THREADS / (2K) threads, then combined in order
-    constexpr int NS = 2 * K;
-    constexpr int PER = SM_THREADS / NS > 0 ? SM_THREADS / NS : 1;
-    __shared__ double red[SM_THREADS];
-    const int t = threadIdx.x;
-    const int stat = t % NS;
-    const int sub = t / NS;
-    // eight interleaved accumulators keep eight loads in flight; the order of
-    // the additions depends only on nblocks, so results are reproducible
-    double acc = 0.0;
-    if (sub < PER) {
-        double a[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) a[u] = 0.0;
-        int b = sub;
-        for (; b + 7 * PER < nblocks; b += 8 * PER) {
-#pragma unroll
-            for (int u = 0; u < 8; ++u) a[u] += __ldcg(part + (int64_t)(b + u * PER) * NS + stat);
-        }
-        for (; b < nblocks; b += PER) a[0] += __ldcg(part + (int64_t)b * NS + stat);
-        acc = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
-    }
-    red[t] = acc;
-    __syncthreads();
-    if (t < NS) {
-        double s = 0.0;
-        for (int j = 0; j < PER; ++j) s += red[j * NS + t];
-        red[t] = s;
-    }
-    __syncthreads();
-    if (t < K) {
-        double s1 = red[t], s2 = red[K + t];
-        double mu = s1 / (double)n;
-        double var = s2 - (double)n * mu * mu;
-        double sd = var > 0.0 ? sqrt(var) : 0.0;
-        stats_out[t] = mu;
-        stats_out[K + t] = sd > 0.0 ? 1.0 / sd : 1.0;
-    }
-}
-
 // Block-level combine of per-lane column sums; lane l of segment 0 with
 // t == 0 holds chunk l.  Writes the block partial and, in the last block to
 // finish, the final statistics.
@@ -101,8 +59,23 @@ __device__ void block_stats(Acc (&s1)[E], Acc (&s2)[E], double* __restrict__ par
     __syncthreads();
     if (last) {
         __threadfence();
-        finish_stats<K>(part, gridDim.x, n, stats_out);
+        finish_stats<K, SM_THREADS>(part, gridDim.x, n, stats_out);
         if (threadIdx.x == 0) *counter = 0u;
+    }
+}
+
+// Column sums of a stored block, per lane in the accumulator type (FP32 for
+// FP32 / BF16 blocks): a lane sums a few hundred entries at most, then lanes
+// are combined in FP32 within a warp and in FP64 from the warp level up.
+// Compensated FP32 sums per lane were measured 13-74 % slower on the
+// latency-bound sweep, and FP64 arithmetic runs at a small fraction of the
+// FP32 rate on this part, so the per-lane sums stay plain FP32.
+template <typename Acc, int E>
+__device__ __forceinline__ void add_sums(Acc (&s1)[E], Acc (&s2)[E], const Acc (&y)[E]) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        s1[e] += y[e];
+        s2[e] += y[e] * y[e];
     }
 }
 
@@ -203,11 +176,7 @@ __global__ void __launch_bounds__(SM_THREADS) k_init(int64_t n, uint64_t seed, u
                 zs += SM_GAMMA;
             }
             store_chunk<T, E>(A + row * K + q * E, x);
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-                s1[e] += x[e];
-                s2[e] += x[e] * x[e];
-            }
+            add_sums<Acc, E>(s1, s2, x);
         }
     }
     block_stats<Acc, K, E, G, GP>(s1, s2, part, counter, n, stats_out);
@@ -227,103 +196,6 @@ static int init_grid(const gr_ctx* c, int64_t n) {
     const int64_t want = ceil_div(n, (int64_t)SM_WARPS * (32 / GP));
     const int64_t cap = (int64_t)c->num_sms * occ;
     return (int)(want < cap ? (want > 0 ? want : 1) : cap);
-}
-
-// ---------------------------------------------------------------------------
-// One sweep: Y = (J A - mu) * inv_s with J A = (1-w) A + w D^-1 A A.
-// LPR lanes serve one row: GP chunk lanes times TS neighbour slots in flight.
-// The row's slot list is read LPR entries at a time (coalesced) and handed
-// out by shuffles; each neighbour row is gathered chunk-wise (16 B / lane).
-// ---------------------------------------------------------------------------
-template <typename T, int K, int LPR>
-__global__ void __launch_bounds__(SM_THREADS) k_sweep(
-    int64_t n, const int64_t* __restrict__ rowptr, const int2* __restrict__ cw32,
-    const int32_t* __restrict__ col, const double* __restrict__ wn64, const T* __restrict__ Ain,
-    T* __restrict__ Aout, double omega_d, const double* __restrict__ stats_in,
-    double* __restrict__ part, unsigned* __restrict__ counter, double* __restrict__ stats_out) {
-    using L = RowLayout<T, K>;
-    using Acc = typename AccOf<T>::type;
-    constexpr int E = L::E, G = L::G, GP = L::GP;
-    static_assert(LPR >= GP && LPR <= 32, "lanes per row");
-    constexpr int TS = LPR / GP;
-    constexpr int RPW = 32 / LPR;
-    constexpr bool F64 = sizeof(T) == 8;
-    const int lane = threadIdx.x & 31;
-    const int seg = lane / LPR, l = lane % LPR;
-    const int q = l % GP, t = l / GP;
-    const unsigned segmask = LPR == 32 ? 0xffffffffu : (((1u << LPR) - 1u) << (seg * LPR));
-    const bool chunk_ok = q < G;
-    const Acc omega = (Acc)omega_d, one_m = (Acc)(1.0 - omega_d);
-
-    Acc mu[E], is[E], s1[E], s2[E];
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-        int k = chunk_ok ? q * E + e : 0;
-        mu[e] = (Acc)stats_in[k];
-        is[e] = (Acc)stats_in[K + k];
-        s1[e] = s2[e] = Acc(0);
-    }
-
-    const int64_t warp_global = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t r0 = warp_global * RPW; r0 < n; r0 += nwarps * RPW) {
-        const int64_t row = r0 + seg;
-        const bool row_ok = row < n;
-        const int64_t b = row_ok ? rowptr[row] : 0;
-        const int64_t e_end = row_ok ? rowptr[row + 1] : 0;
-        Acc acc[E];
-#pragma unroll
-        for (int e = 0; e < E; ++e) acc[e] = Acc(0);
-        for (int64_t base = b; base < e_end; base += LPR) {
-            const int64_t j = base + l;
-            int cj = 0;
-            Acc wj = Acc(0);
-            if (j < e_end) {
-                if constexpr (F64) {
-                    cj = col[j];
-                    wj = (Acc)wn64[j];
-                } else {
-                    int2 v = cw32[j];
-                    cj = v.x;
-                    wj = (Acc)__int_as_float(v.y);
-                }
-            }
-            const int cnt = (int)min((int64_t)LPR, e_end - base);
-#pragma unroll
-            for (int r = 0; r < GP; ++r) {
-                const int src = r * TS + t;
-                const int c = __shfl_sync(segmask, cj, src, LPR);
-                const Acc w = __shfl_sync(segmask, wj, src, LPR);
-                if (src < cnt && chunk_ok) {
-                    Acc x[E];
-                    load_chunk<T, E>(Ain + (int64_t)c * K + q * E, x);
-#pragma unroll
-                    for (int e = 0; e < E; ++e) acc[e] = fma(w, x[e], acc[e]);
-                }
-            }
-        }
-#pragma unroll
-        for (int e = 0; e < E; ++e)
-#pragma unroll
-            for (int o = GP; o < LPR; o <<= 1) acc[e] += __shfl_xor_sync(segmask, acc[e], o, LPR);
-        if (row_ok && t == 0 && chunk_ok) {
-            Acc xi[E], y[E];
-            load_chunk<T, E>(Ain + row * K + q * E, xi);
-            const bool isolated = b == e_end;
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-                Acc z = isolated ? xi[e] : one_m * xi[e] + omega * acc[e];
-                y[e] = (z - mu[e]) * is[e];
-            }
-            store_chunk<T, E>(Aout + row * K + q * E, y);
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-                s1[e] += y[e];
-                s2[e] += y[e] * y[e];
-            }
-        }
-    }
-    block_stats<Acc, K, E, G, LPR>(s1, s2, part, counter, n, stats_out);
 }
 
 // ---------------------------------------------------------------------------
@@ -491,13 +363,9 @@ __global__ void __launch_bounds__(SM_THREADS) k_sweep_stream(
                         y[e] = (z - st_sh[k]) * st_sh[K + k];
                     }
                     store_chunk<T, E>(Aout + (int64_t)row * K + q * E, y);
-#pragma unroll
-                    for (int e = 0; e < E; ++e) {
-                        s1[e] += y[e];
-                        s2[e] += y[e] * y[e];
-                    }
+                    add_sums<Acc, E>(s1, s2, y);
                 }
-                gb = e_end;
+                        gb = e_end;
             }
         }
         cp_async_wait_all();
@@ -558,10 +426,11 @@ __device__ void block_stats_rows(Acc (&s1)[E], Acc (&s2)[E], double* __restrict_
     __syncthreads();
     if (last) {
         __threadfence();
-        finish_stats<K>(part, gridDim.x, n, stats_out);
+        finish_stats<K, SM_THREADS>(part, gridDim.x, n, stats_out);
         if (threadIdx.x == 0) *counter = 0u;
     }
 }
+
 
 template <typename T, int K, int U>
 __global__ void __launch_bounds__(SM_THREADS) k_sweep_row(
@@ -625,6 +494,17 @@ __global__ void __launch_bounds__(SM_THREADS) k_sweep_row(
                         for (int e = 0; e < E; ++e) acc[e] = fma(w, x[u][e], acc[e]);
                     }
             }
+#ifndef GR_NO_SLOT_PF
+            if (q == 0 && e1 > b1) {
+                // the next group's slot lines into L1 (its row pointers have
+                // arrived by now): its slot loads then wait on L1, not on
+                // memory, and no register is held for them
+                const char* p0 = reinterpret_cast<const char*>(slots + b1);
+                const char* p1 = reinterpret_cast<const char*>(slots + e1) - 1;
+                asm volatile("prefetch.global.L1 [%0];" ::"l"(p0));
+                if (((uintptr_t)p0 >> 7) != ((uintptr_t)p1 >> 7)) asm volatile("prefetch.global.L1 [%0];" ::"l"(p1));
+            }
+#endif
             if (row < n) {
                 const bool isolated = b0 == e0;
                 Acc y[E];
@@ -635,11 +515,7 @@ __global__ void __launch_bounds__(SM_THREADS) k_sweep_row(
                     y[e] = (z - st_sh[k]) * st_sh[K + k];
                 }
                 store_chunk<T, E>(Aout + (size_t)row * K + q * E, y);
-#pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    s1[e] += y[e];
-                    s2[e] += y[e] * y[e];
-                }
+                add_sums<Acc, E>(s1, s2, y);
             }
         }
         b0 = b1;
@@ -650,11 +526,11 @@ __global__ void __launch_bounds__(SM_THREADS) k_sweep_row(
     block_stats_rows<Acc, K, E, G>(s1, s2, part, counter, n64, stats_out);
 }
 
-// X = (A - mu) * inv_s, chunk-parallel.  The statistics are converted to the
+// X = (A - mu) * inv_s, chunk-parallel; A may be X itself (each entry is read
+// and written by the same thread).  The statistics are converted to the
 // accumulator type once per block; chunk indices are 32-bit when they fit.
 template <typename T, int K>
-__global__ void k_apply(int64_t n, const T* __restrict__ A, T* __restrict__ X,
-                        const double* __restrict__ stats) {
+__global__ void k_apply(int64_t n, const T* A, T* X, const double* __restrict__ stats) {
     using L = RowLayout<T, K>;
     using Acc = typename AccOf<T>::type;
     constexpr int E = L::E, G = L::G;
@@ -684,18 +560,25 @@ __global__ void k_apply(int64_t n, const T* __restrict__ A, T* __restrict__ X,
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
-template <typename T, int K, int LPR>
-static cudaError_t launch_sweep(gr_ctx* c, int grid, const T* Ain, T* Aout, double omega,
-                                const double* st_in, double* part, unsigned* counter,
-                                double* st_out) {
-    k_sweep<T, K, LPR><<<grid, SM_THREADS, 0, c->stream>>>(c->n, c->rowptr, c->cw32, c->col, c->wn64,
-                                                          Ain, Aout, omega, st_in, part, counter,
-                                                          st_out); count_launch();
-    return cudaGetLastError();
-}
+// Scratch the sweep launchers keep in the context between calls (the packed
+// FP64 slots, the streaming kernel's row partition).  graph_reduce_smooth
+// allocates it in the context on first use; the allocation-free entry point
+// passes a region of its fixed array instead, and whatever the context does
+// not hold already is rebuilt there on every call.
+struct SweepScratch {
+    char* base = nullptr;  // nullptr: allocate in the context
+    size_t bytes = 0, used = 0;
+    bool fixed() const { return base != nullptr; }
+    void* take(size_t n) {
+        const size_t off = (used + 255) & ~size_t(255);
+        if (off + n > bytes) return nullptr;
+        used = off + n;
+        return base + off;
+    }
+};
 
 // Streaming sweep when a group of 32 / GP rows would hold more slots than
-// four ring batches (long rows); the row-group kernel otherwise.
+// four ring batches (long rows).
 template <typename T, int K>
 static bool stream_wide(const gr_ctx* c) {
     constexpr int GP = RowLayout<T, K>::GP;
@@ -703,61 +586,99 @@ static bool stream_wide(const gr_ctx* c) {
     return GP < 32 && (32.0 / GP) * avg > 128.0;
 }
 
-template <typename T, int K, int LPR>
-static cudaError_t stream_occupancy(int* blocks_per_sm, size_t* dyn) {
-    using Slot = typename SlotOf<T>::type;
-    *dyn = sizeof(Slot) * (size_t)ST_RING * SM_WARPS;
-    static int cached = 0;
-    if (!cached) {
-        auto kern = k_sweep_stream<T, K, LPR>;
-        GR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*dyn));
-        GR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cached, kern, SM_THREADS, *dyn));
-        if (cached < 1) cached = 1;
-    }
-    *blocks_per_sm = cached;
-    return cudaSuccess;
+template <typename T>
+constexpr int prec_of() {
+    return sizeof(T) == 8 ? GR_F64 : (sizeof(T) == 4 ? GR_F32 : GR_BF16);
 }
 
-template <typename T, int K, int LPR>
-static cudaError_t launch_sweep_stream_lpr(gr_ctx* c, const T* Ain, T* Aout, double omega, const double* st_in,
-                                           double* part, int part_cap, unsigned* counter, double* st_out) {
-    int bps = 1;
+// the kernel every sweep of one smoothing call runs, and its inputs
+struct SweepPlan {
+    int kind = GR_SWEEP_ROW;     // GR_SWEEP_ROW / GR_SWEEP_STREAM
+    const int4* cw64 = nullptr;  // FP64 slots of the row-group and streaming kernels
+    const int32_t* wpart = nullptr;
+    int grid = 0;
     size_t dyn = 0;
-    GR_CUDA((stream_occupancy<T, K, LPR>(&bps, &dyn)));
-    int grid = c->num_sms * bps;
-    if (grid > part_cap) grid = part_cap;
-    const int64_t W = (int64_t)grid * SM_WARPS;
-    if (c->wpart_W != W) {
-        if (c->wpart) GR_CUDA(cudaFreeAsync(c->wpart, c->stream));
-        c->wpart = nullptr;
-        c->wpart_W = 0;
-        GR_CUDA(cudaMallocAsync(&c->wpart, sizeof(int32_t) * (size_t)(W + 1), c->stream));
-        k_warp_partition<<<(unsigned)ceil_div(W + 1, 256), 256, 0, c->stream>>>(c->n, c->rowptr, W, c->wpart);
-        count_launch();
-        c->wpart_W = W;
+};
+
+// packed (column, 0, FP64 weight) slots
+static cudaError_t prepare_slots64(gr_ctx* c, SweepScratch& sc, const int4** out) {
+    if (c->cw64) {
+        *out = c->cw64;
+        return cudaSuccess;
     }
-    const typename SlotOf<T>::type* slots;
-    if constexpr (sizeof(T) == 8) {
-        if (!c->cw64) {
-            GR_CUDA(cudaMallocAsync(&c->cw64, sizeof(int4) * (size_t)(2 * c->m > 0 ? 2 * c->m : 1), c->stream));
-            if (c->m > 0) {
-                k_pack64<<<(unsigned)ceil_div(2 * c->m, 256), 256, 0, c->stream>>>(2 * c->m, c->col, c->wn64, c->cw64);
-                count_launch();
-            }
-        }
-        slots = c->cw64;
+    const size_t bytes = sizeof(int4) * (size_t)(2 * c->m > 0 ? 2 * c->m : 1);
+    int4* p = nullptr;
+    if (sc.fixed()) {
+        p = (int4*)sc.take(bytes);
+        if (!p) return cudaErrorMemoryAllocation;
     } else {
-        slots = c->cw32;
+        GR_CUDA(cudaMallocAsync(&c->cw64, bytes, c->stream));
+        p = c->cw64;
     }
-    k_sweep_stream<T, K, LPR><<<grid, SM_THREADS, dyn, c->stream>>>(c->n, c->rowptr, slots, 2 * c->m, c->wpart,
-                                                                   Ain, Aout, omega, st_in, part, counter, st_out);
-    count_launch();
+    if (c->m > 0) {
+        k_pack64<<<(unsigned)ceil_div(2 * c->m, 256), 256, 0, c->stream>>>(2 * c->m, c->col, c->wn64, p);
+        count_launch();
+    }
+    *out = p;
     return cudaGetLastError();
 }
 
 template <typename T, int K>
-static cudaError_t launch_sweep_row(gr_ctx* c, const T* Ain, T* Aout, double omega, const double* st_in,
-                                    double* part, int part_cap, unsigned* counter, double* st_out) {
+static cudaError_t prepare_stream(gr_ctx* c, SweepScratch& sc, int part_cap, SweepPlan* P) {
+    using Slot = typename SlotOf<T>::type;
+    static int bps = 0;
+    P->dyn = sizeof(Slot) * (size_t)ST_RING * SM_WARPS;
+    if (!bps) {
+        auto kern = k_sweep_stream<T, K, 32>;
+        GR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P->dyn));
+        GR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, SM_THREADS, P->dyn));
+        if (bps < 1) bps = 1;
+    }
+    int grid = c->num_sms * bps;
+    if (grid > part_cap) grid = part_cap;
+    P->grid = grid;
+    const int64_t W = (int64_t)grid * SM_WARPS;
+    if (c->wpart_W == W) {
+        P->wpart = c->wpart;
+    } else {
+        int32_t* wp = nullptr;
+        if (sc.fixed()) {
+            wp = (int32_t*)sc.take(sizeof(int32_t) * (size_t)(W + 1));
+            if (!wp) return cudaErrorMemoryAllocation;
+        } else {
+            if (c->wpart) GR_CUDA(cudaFreeAsync(c->wpart, c->stream));
+            c->wpart = nullptr;
+            c->wpart_W = 0;
+            GR_CUDA(cudaMallocAsync(&c->wpart, sizeof(int32_t) * (size_t)(W + 1), c->stream));
+            c->wpart_W = W;
+            wp = c->wpart;
+        }
+        k_warp_partition<<<(unsigned)ceil_div(W + 1, 256), 256, 0, c->stream>>>(c->n, c->rowptr, W, wp);
+        count_launch();
+        P->wpart = wp;
+    }
+    if constexpr (sizeof(T) == 8) GR_CUDA(prepare_slots64(c, sc, &P->cw64));
+    return cudaGetLastError();
+}
+
+// Kernel choice: forced by graph_reduce_set_sweep_kernel, or rows long enough
+// to fill a warp -> streaming kernel, otherwise the row-group kernel.
+template <typename T, int K>
+static cudaError_t sweep_prepare(gr_ctx* c, SweepScratch& sc, int part_cap, SweepPlan* P) {
+    const int want = c->sweep_kind;
+    if (want == GR_SWEEP_STREAM || (want == GR_SWEEP_AUTO && stream_wide<T, K>(c))) {
+        P->kind = GR_SWEEP_STREAM;
+        return prepare_stream<T, K>(c, sc, part_cap, P);
+    }
+    P->kind = GR_SWEEP_ROW;
+    if constexpr (sizeof(T) == 8) GR_CUDA(prepare_slots64(c, sc, &P->cw64));
+    return cudaSuccess;
+}
+
+template <typename T, int K>
+static cudaError_t launch_sweep_row(gr_ctx* c, const SweepPlan& P, const T* Ain, T* Aout, double omega,
+                                    const double* st_in, double* part, int part_cap, unsigned* counter,
+                                    double* st_out) {
     // two slots in flight per lane; four on rows of mean degree >= 10 in
     // FP32/BF16 storage (measured: 13-19 % faster there, slower in FP64 and
     // on shorter rows).  The products are added in slot order either way.
@@ -772,18 +693,8 @@ static cudaError_t launch_sweep_row(gr_ctx* c, const T* Ain, T* Aout, double ome
     int grid = c->num_sms * (four ? bps4 : bps2);
     if (grid > part_cap) grid = part_cap;
     const typename SlotOf<T>::type* slots;
-    if constexpr (sizeof(T) == 8) {
-        if (!c->cw64) {
-            GR_CUDA(cudaMallocAsync(&c->cw64, sizeof(int4) * (size_t)(2 * c->m > 0 ? 2 * c->m : 1), c->stream));
-            if (c->m > 0) {
-                k_pack64<<<(unsigned)ceil_div(2 * c->m, 256), 256, 0, c->stream>>>(2 * c->m, c->col, c->wn64, c->cw64);
-                count_launch();
-            }
-        }
-        slots = c->cw64;
-    } else {
-        slots = c->cw32;
-    }
+    if constexpr (sizeof(T) == 8) slots = P.cw64;
+    else slots = c->cw32;
     if (four)
         k_sweep_row<T, K, 4><<<grid, SM_THREADS, 0, c->stream>>>(c->n, c->rowptr, slots, Ain, Aout, omega, st_in, part,
                                                                  counter, st_out);
@@ -794,51 +705,46 @@ static cudaError_t launch_sweep_row(gr_ctx* c, const T* Ain, T* Aout, double ome
     return cudaGetLastError();
 }
 
-// Sweep kernel choice: rows long enough to fill a warp -> streaming kernel;
-// short rows -> row-group kernel.
 template <typename T, int K>
-static cudaError_t launch_sweep_best(gr_ctx* c, const T* Ain, T* Aout, double omega, const double* st_in,
-                                     double* part, int part_cap, unsigned* counter, double* st_out) {
-    if (stream_wide<T, K>(c))
-        return launch_sweep_stream_lpr<T, K, 32>(c, Ain, Aout, omega, st_in, part, part_cap, counter, st_out);
-    return launch_sweep_row<T, K>(c, Ain, Aout, omega, st_in, part, part_cap, counter, st_out);
+static cudaError_t launch_sweep(gr_ctx* c, const SweepPlan& P, const T* Ain, T* Aout, double omega,
+                                const double* st_in, double* part, int part_cap, unsigned* counter, double* st_out) {
+    if (P.kind == GR_SWEEP_STREAM) {
+        const typename SlotOf<T>::type* slots;
+        if constexpr (sizeof(T) == 8) slots = P.cw64;
+        else slots = c->cw32;
+        k_sweep_stream<T, K, 32><<<P.grid, SM_THREADS, P.dyn, c->stream>>>(c->n, c->rowptr, slots, 2 * c->m, P.wpart,
+                                                                          Ain, Aout, omega, st_in, part, counter,
+                                                                          st_out);
+        count_launch();
+        return cudaGetLastError();
+    }
+    return launch_sweep_row<T, K>(c, P, Ain, Aout, omega, st_in, part, part_cap, counter, st_out);
 }
 
-template <typename T, int K>
-static int pick_lpr(const gr_ctx* c) {
-    constexpr int GP = RowLayout<T, K>::GP;
-    double avg = c->n > 0 ? 2.0 * (double)c->m / (double)c->n : 0.0;
-    int ts = 1;
-    while (ts * GP < 32 && ts * 4 <= avg) ts *= 2;  // at least two neighbours per sub-slot
-    return ts * GP;
+// Bytes of the statistics region: two 2K-double statistics sets and the
+// last-block counter.
+template <int K>
+constexpr size_t stats_bytes() {
+    return sizeof(double) * 4 * K + 64;
 }
 
+// X0, `sweeps` sweeps and the final centring + scaling into X.  buf is the
+// second n x K block; stats has stats_bytes<K>(); part holds 2K doubles for
+// each of up to part_cap blocks.
 template <typename T, int K>
-static cudaError_t run_smooth(gr_ctx* c, int sweeps, double omega, uint64_t seed, int level,
-                              T* X, cudaEvent_t ev0, cudaEvent_t ev1) {
+static cudaError_t run_sweeps(gr_ctx* c, SweepScratch& sc, int sweeps, double omega, uint64_t seed, int level,
+                              T* X, T* buf, double* stats, double* part, int part_cap, cudaEvent_t ev0,
+                              cudaEvent_t ev1) {
     cudaStream_t s = c->stream;
     const int64_t n = c->n;
-    constexpr int GP = RowLayout<T, K>::GP;
-    void *p_buf, *p_st, *p_part;
-    GR_CUDA(c->ws.get(WS_SMOOTH_BUF, sizeof(T) * (size_t)n * K, &p_buf));
-    GR_CUDA(c->ws.get(WS_SMOOTH_STATS, sizeof(double) * 4 * K + 64, &p_st));
-    T* buf = (T*)p_buf;
-    double* st0 = (double*)p_st;
+    double* st0 = stats;
     double* st1 = st0 + 2 * K;
     unsigned* counter = (unsigned*)(st1 + 2 * K);
-    const int lpr = pick_lpr<T, K>(c);
-    const int rows_per_block = SM_WARPS * (32 / lpr);
-    const int64_t want = ceil_div(n, rows_per_block);
-    const int64_t cap = (int64_t)c->num_sms * 8;
-    const int grid = (int)(want < cap ? (want > 0 ? want : 1) : cap);
-    const int igrid = init_grid<T, K>(c, n);
-    // the streaming sweep runs a persistent grid of at most 8 blocks per SM
-    int maxgrid = grid > igrid ? grid : igrid;
-    if (c->num_sms * 8 > maxgrid) maxgrid = c->num_sms * 8;
-    GR_CUDA(c->ws.get(WS_SMOOTH_PART, sizeof(double) * 2 * K * (size_t)maxgrid, &p_part));
-    double* part = (double*)p_part;
+    // the counter must start at zero: the region may hold an earlier call's values
     GR_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned), s));
-
+    SweepPlan P;
+    if (sweeps > 0) GR_CUDA((sweep_prepare<T, K>(c, sc, part_cap, &P)));
+    const int igrid = init_grid<T, K>(c, n);
     k_init<T, K><<<igrid, SM_THREADS, 0, s>>>(n, seed, (uint64_t)level, X, part, counter, st0); count_launch();
     GR_CUDA(cudaGetLastError());
     const T* cur = X;
@@ -847,7 +753,7 @@ static cudaError_t run_smooth(gr_ctx* c, int sweeps, double omega, uint64_t seed
     double* sin = st0;
     double* sout = st1;
     for (int it = 0; it < sweeps; ++it) {
-        GR_CUDA((launch_sweep_best<T, K>(c, cur, nxt, omega, sin, part, maxgrid, counter, sout)));
+        GR_CUDA((launch_sweep<T, K>(c, P, cur, nxt, omega, sin, part, part_cap, counter, sout)));
         const T* tmp = cur;
         cur = nxt;
         nxt = (T*)tmp;
@@ -862,6 +768,23 @@ static cudaError_t run_smooth(gr_ctx* c, int sweeps, double omega, uint64_t seed
         count_launch();
     }
     return cudaGetLastError();
+}
+
+// blocks any sweep or k_init grid may have (the statistics partials)
+static int part_capacity(const gr_ctx* c) { return c->num_sms * 8; }
+
+template <typename T, int K>
+static cudaError_t run_smooth(gr_ctx* c, int sweeps, double omega, uint64_t seed, int level,
+                              T* X, cudaEvent_t ev0, cudaEvent_t ev1) {
+    const int64_t n = c->n;
+    void *p_buf, *p_st, *p_part;
+    const int cap = part_capacity(c);
+    GR_CUDA(c->ws.get(WS_SMOOTH_BUF, sizeof(T) * (size_t)n * K, &p_buf));
+    GR_CUDA(c->ws.get(WS_SMOOTH_STATS, stats_bytes<K>(), &p_st));
+    GR_CUDA(c->ws.get(WS_SMOOTH_PART, sizeof(double) * 2 * K * (size_t)cap, &p_part));
+    SweepScratch sc;
+    return run_sweeps<T, K>(c, sc, sweeps, omega, seed, level, X, (T*)p_buf, (double*)p_st, (double*)p_part, cap,
+                            ev0, ev1);
 }
 
 template <typename T>
@@ -930,6 +853,39 @@ gr_status smooth_impl(gr_ctx* c, int K, int sweeps, double omega, uint64_t seed,
         default: return set_error(c, GR_EINVAL, "smooth: unknown precision");
     }
     if (e != cudaSuccess) return cuda_error(c, e, "smooth");
+    return GR_OK;
+}
+
+// The kernel choice of sweep_prepare, without launching or allocating.
+template <typename T, int K>
+static cudaError_t sweep_plan_typed(gr_ctx* c, int32_t* kind) {
+    const int want = c->sweep_kind;
+    *kind = (want == GR_SWEEP_STREAM || (want == GR_SWEEP_AUTO && stream_wide<T, K>(c))) ? GR_SWEEP_STREAM
+                                                                                         : GR_SWEEP_ROW;
+    return cudaSuccess;
+}
+
+template <typename T>
+static cudaError_t sweep_plan_k(gr_ctx* c, int K, int32_t* info) {
+    switch (K) {
+        case 4: return sweep_plan_typed<T, 4>(c, info);
+        case 8: return sweep_plan_typed<T, 8>(c, info);
+        case 16: return sweep_plan_typed<T, 16>(c, info);
+        case 24: return sweep_plan_typed<T, 24>(c, info);
+        case 32: return sweep_plan_typed<T, 32>(c, info);
+    }
+    return cudaErrorInvalidValue;
+}
+
+gr_status sweep_plan_impl(gr_ctx* c, int K, gr_prec prec, int32_t* info) {
+    cudaError_t e;
+    switch (prec) {
+        case GR_F64: e = sweep_plan_k<double>(c, K, info); break;
+        case GR_F32: e = sweep_plan_k<float>(c, K, info); break;
+        case GR_BF16: e = sweep_plan_k<__nv_bfloat16>(c, K, info); break;
+        default: return set_error(c, GR_EINVAL, "sweep_plan: unknown precision");
+    }
+    if (e != cudaSuccess) return cuda_error(c, e, "sweep_plan");
     return GR_OK;
 }
 
@@ -1125,11 +1081,7 @@ __global__ void __launch_bounds__(SM_THREADS) k_col_stats(int64_t n, const T* __
         if (row < n && q < G) {
             Acc x[E];
             load_chunk<T, E>(A + row * K + q * E, x);
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-                s1[e] += x[e];
-                s2[e] += x[e] * x[e];
-            }
+            add_sums<Acc, E>(s1, s2, x);
         }
     }
     block_stats<Acc, K, E, G, GP>(s1, s2, part, counter, n, stats_out);
@@ -1291,20 +1243,13 @@ static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 template <typename T, int K>
 static gr_status run_smooth_noalloc(gr_ctx* c, int sweeps, double omega, uint64_t seed, int level,
                                     T* X) {
-    cudaStream_t s = c->stream;
     const int64_t n = c->n;
-    constexpr int GP = RowLayout<T, K>::GP;
-    const int lpr = pick_lpr<T, K>(c);
-    const int rows_per_block = SM_WARPS * (32 / lpr);
-    const int64_t cap = (int64_t)c->num_sms * 8;
-    const int64_t want = ceil_div(n, rows_per_block);
-    const int grid = (int)(want < cap ? (want > 0 ? want : 1) : cap);
-    const int igrid = init_grid<T, K>(c, n);
-    const int maxgrid = grid > igrid ? grid : igrid;
-    // layout of the shared scratch: [vector block | 2 x 2K stats + counter | partials]
+    const int cap = part_capacity(c);
+    // layout of the fixed array: [second vector block | statistics | partials |
+    // launcher scratch (packed FP64 slots, row partition) the context lacks]
     const size_t b_buf = align256(sizeof(T) * (size_t)n * K);
-    const size_t b_st = align256(sizeof(double) * 4 * K + 64);
-    const size_t b_part = align256(sizeof(double) * 2 * K * (size_t)maxgrid);
+    const size_t b_st = align256(stats_bytes<K>());
+    const size_t b_part = align256(sizeof(double) * 2 * K * (size_t)cap);
     if (b_buf + b_st + b_part > NOALLOC_SCRATCH_BYTES)
         return set_error(c, GR_EINVAL,
                          "smooth_noalloc: n*K*sizeof(element) plus statistics exceeds the 32 MiB "
@@ -1313,44 +1258,16 @@ static gr_status run_smooth_noalloc(gr_ctx* c, int sweeps, double omega, uint64_
     cudaError_t e = noalloc_scratch_addr(c->device, &base);
     if (e != cudaSuccess) return cuda_error(c, e, "smooth_noalloc: scratch address");
     char* B = (char*)base;
-    T* buf = (T*)B;
-    double* st0 = (double*)(B + b_buf);
-    double* st1 = st0 + 2 * K;
-    unsigned* counter = (unsigned*)(st1 + 2 * K);
-    double* part = (double*)(B + b_buf + b_st);
-    // the array keeps the previous call's contents: the last-block counter
-    // must start at zero
-    GR_TRY_CUDA(c, cudaMemsetAsync(counter, 0, sizeof(unsigned), s), "smooth_noalloc");
-    k_init<T, K><<<igrid, SM_THREADS, 0, s>>>(n, seed, (uint64_t)level, X, part, counter, st0);
-    count_launch();
-    GR_TRY_CUDA(c, cudaGetLastError(), "smooth_noalloc: init");
-    const T* cur = X;
-    T* nxt = buf;
-    double* sin = st0;
-    double* sout = st1;
-    for (int it = 0; it < sweeps; ++it) {
-        switch (lpr / GP) {
-            case 1: e = launch_sweep<T, K, GP>(c, grid, cur, nxt, omega, sin, part, counter, sout); break;
-            case 2: e = launch_sweep<T, K, (2 * GP <= 32 ? 2 * GP : 32)>(c, grid, cur, nxt, omega, sin, part, counter, sout); break;
-            case 4: e = launch_sweep<T, K, (4 * GP <= 32 ? 4 * GP : 32)>(c, grid, cur, nxt, omega, sin, part, counter, sout); break;
-            case 8: e = launch_sweep<T, K, (8 * GP <= 32 ? 8 * GP : 32)>(c, grid, cur, nxt, omega, sin, part, counter, sout); break;
-            case 16: e = launch_sweep<T, K, (16 * GP <= 32 ? 16 * GP : 32)>(c, grid, cur, nxt, omega, sin, part, counter, sout); break;
-            default: e = launch_sweep<T, K, 32>(c, grid, cur, nxt, omega, sin, part, counter, sout); break;
-        }
-        if (e != cudaSuccess) return cuda_error(c, e, "smooth_noalloc: sweep");
-        const T* tmp = cur;
-        cur = nxt;
-        nxt = (T*)tmp;
-        double* ts = sin;
-        sin = sout;
-        sout = ts;
-    }
-    constexpr int G = RowLayout<T, K>::G;
-    if (n > 0) {
-        k_apply<T, K><<<(unsigned)ceil_div(n * G, 256), 256, 0, s>>>(n, cur, X, sin);
-        count_launch();
-    }
-    GR_TRY_CUDA(c, cudaGetLastError(), "smooth_noalloc: apply");
+    SweepScratch sc;
+    sc.base = B + b_buf + b_st + b_part;
+    sc.bytes = NOALLOC_SCRATCH_BYTES - (b_buf + b_st + b_part);
+    e = run_sweeps<T, K>(c, sc, sweeps, omega, seed, level, X, (T*)B, (double*)(B + b_buf),
+                         (double*)(B + b_buf + b_st), cap, nullptr, nullptr);
+    if (e == cudaErrorMemoryAllocation)
+        return set_error(c, GR_EINVAL,
+                         "smooth_noalloc: the packed FP64 slots or the row partition of this graph do not "
+                         "fit the rest of the 32 MiB allocation-free scratch");
+    if (e != cudaSuccess) return cuda_error(c, e, "smooth_noalloc");
     return GR_OK;
 }
 

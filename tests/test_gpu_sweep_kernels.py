@@ -1,0 +1,141 @@
+"""GPU parity of both sweep kernels (Alg. 3 weighted-Jacobi sweeps, Sec.
+3.2.1) against the FP64 oracle: each kernel is forced on each graph family
+through graph_reduce_set_sweep_kernel, and the automatic choice is checked.
+
+Bars as for graph_reduce_smooth: per-column |dX|/|X| <= 1e-12 in FP64 and
+<= 1e-5 in FP32.  The families mix short and long rows, a hub row, random
+long edges, isolated rows and dense graphs, so each kernel meets rows of
+every length.
+"""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def gr():
+    from paper_1812_08942_gb300 import build as B
+    B.build()
+    import paper_1812_08942_gb300 as gr
+    gr.load()
+    return gr
+
+
+def _col_relerr(A, B):
+    A = np.asarray(A, np.float64)
+    B = np.asarray(B, np.float64)
+    return np.linalg.norm(A - B, axis=0) / np.maximum(np.linalg.norm(B, axis=0), 1e-300)
+
+
+def _grid_plus(a, b, extra, hub_deg, seed):
+    """a x b grid plus `extra` random long edges and one hub joined to
+    hub_deg nodes: mostly local, with rows whose neighbours leave any window
+    and one row whose slots overflow a band."""
+    g = W.grid2d(a, b)
+    rng = np.random.default_rng(seed)
+    n = g.n
+    u = [g.u.astype(np.int64)]
+    v = [g.v.astype(np.int64)]
+    p = rng.integers(0, n, extra)
+    q = rng.integers(0, n, extra)
+    u.append(p)
+    v.append(q)
+    hub = n // 2
+    nb = rng.choice(n, hub_deg, replace=False)
+    u.append(np.full(hub_deg, hub))
+    v.append(nb)
+    uu = np.concatenate(u)
+    vv = np.concatenate(v)
+    w = rng.lognormal(0.0, 0.5, len(uu))
+    cu, cv, cw = W.canonicalize(n, uu, vv, w)
+    return W.Graph(n, cu, cv, cw)
+
+
+FAMILIES = {
+    "grid64": lambda: W.grid2d(64, 64),
+    "grid160x120": lambda: W.grid2d(160, 120),
+    "mesh_ln": lambda: W.mesh3d(19, 17, 13, seed=4),
+    "path_iso": lambda: W.Graph(3000, np.arange(0, 2500, dtype=np.int32), np.arange(1, 2501, dtype=np.int32),
+                                np.linspace(0.5, 2.0, 2500)),  # nodes 2501..2999 isolated
+    "grid_long_hub": lambda: _grid_plus(96, 80, 3000, 2500, seed=11),
+    "rand_w": lambda: W.random_sparse(1537, 6000, seed=3),
+    "star": lambda: W.star(300),
+    "complete": lambda: W.complete(40, 0.5),
+}
+
+KINDS = ["ROW", "STREAM", "AUTO"]
+
+
+def _kind(gr, name):
+    return getattr(gr, "GR_SWEEP_" + name)
+
+
+def _smooth(gr, G, n, K, dtype, S, omega, seed, level):
+    X = torch.empty(n, K, dtype=dtype, device=DEV)
+    gr.graph_reduce_smooth(G, X, S, omega, seed, level)
+    return X
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("name", list(FAMILIES))
+def test_sweep_kernels_f64_f32(gr, oracle_mod, kind, name):
+    g = FAMILIES[name]()
+    S, omega, seed, level = 5, 0.7, 5, 1
+    G = gr.graph_reduce_create(g.n, g.u, g.v, g.w)
+    gr.graph_reduce_set_sweep_kernel(G, _kind(gr, kind))
+    for K in (4, 8, 16, 24, 32):
+        ref = oracle_mod.smooth(g.n, g.u, g.v, g.w, K, S, omega, seed, level)
+        for dtype, bar in ((torch.float64, 1e-12), (torch.float32, 1e-5)):
+            plan = gr.graph_reduce_sweep_plan(G, K, dtype)
+            if kind != "AUTO":
+                assert plan == _kind(gr, kind)
+            elif 2 * g.m / g.n < 4:
+                # short rows: the row-group kernel
+                assert plan == gr.GR_SWEEP_ROW, (K, plan)
+            X = _smooth(gr, G, g.n, K, dtype, S, omega, seed, level)
+            err = _col_relerr(X.double().cpu().numpy(), ref).max()
+            assert err <= bar, (name, kind, K, dtype, err, plan)
+
+
+@pytest.mark.parametrize("kind", ["ROW", "STREAM"])
+@pytest.mark.parametrize("K", [16, 24])
+def test_sweep_kernels_large_grid(gr, oracle_mod, kind, K):
+    # 64 x 12288 grid: grids of many blocks, every block several row groups
+    g = W.grid2d(64, 12288)
+    S, omega, seed, level = 6, 0.7, 2, 0
+    ref = oracle_mod.smooth(g.n, g.u, g.v, g.w, K, S, omega, seed, level)
+    G = gr.graph_reduce_create(g.n, g.u, g.v, g.w)
+    gr.graph_reduce_set_sweep_kernel(G, _kind(gr, kind))
+    for dtype, bar in ((torch.float64, 1e-12), (torch.float32, 1e-5)):
+        assert gr.graph_reduce_sweep_plan(G, K, dtype) == _kind(gr, kind)
+        X = _smooth(gr, G, g.n, K, dtype, S, omega, seed, level)
+        err = _col_relerr(X.double().cpu().numpy(), ref).max()
+        assert err <= bar, (kind, K, dtype, err)
+
+
+def test_sweep_kernels_bf16_agree(gr):
+    # BF16 storage: both kernels store the same products in slot order, so
+    # they agree to within a few BF16 roundings
+    g = FAMILIES["grid_long_hub"]()
+    G = gr.graph_reduce_create(g.n, g.u, g.v, g.w)
+    out = {}
+    for kd in ("ROW", "STREAM"):
+        gr.graph_reduce_set_sweep_kernel(G, _kind(gr, kd))
+        assert gr.graph_reduce_sweep_plan(G, 16, torch.bfloat16) == _kind(gr, kd)
+        out[kd] = _smooth(gr, G, g.n, 16, torch.bfloat16, 5, 0.7, 1, 0).float().cpu().numpy()
+    err = _col_relerr(out["STREAM"], out["ROW"]).max()
+    assert err <= 2e-2, err
+
+
+def test_set_sweep_kernel_rejects_unknown(gr):
+    g = W.grid2d(30, 30)
+    G = gr.graph_reduce_create(g.n, g.u, g.v, g.w)
+    with pytest.raises(gr.GraphReduceError) as e:
+        gr.graph_reduce_set_sweep_kernel(G, 17)
+    assert e.value.status == gr.GR_EINVAL
