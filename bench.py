@@ -18,6 +18,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import re
 import statistics
 import subprocess
@@ -32,7 +33,7 @@ if ROOT not in sys.path:
 METRIC = "input edges/s per aggregation level (sum over levels of m_l / step time)"
 UNIT = "edges/s"
 DEFAULT_WORKLOAD = "mesh3d_128"
-# bounded oracle sample: the same Chung-Lu recipe at 1/8 scale
+# bounded oracle sample (reference arm): the same recipe at 1/8 scale
 SAMPLE_DIV = 8
 
 
@@ -87,6 +88,56 @@ def load_peaks():
 # ---------------------------------------------------------------------------
 def sweep_bytes(n, m, K, xbytes, wbytes):
     return 2 * m * (4 + wbytes) + 8 * (n + 1) + 2 * n * K * xbytes
+
+
+def affinity_bytes(n, m, K, xbytes, dbytes):
+    """Per-edge distance: the upper-triangle columns, the block read once, d written."""
+    return m * 4 + n * K * xbytes + m * dbytes
+
+
+def aggregate_bytes(n, m, dbytes, passes=2):
+    """Suitor matching, every pass scanning every CSR slot once (column +
+    key) and updating per-node state (8 bytes)."""
+    return passes * (2 * m * (4 + dbytes) + 8 * n)
+
+
+def galerkin_bytes(n, m, mc):
+    """Galerkin product: the fine edge list (u, v, w) and the map read, the
+    coarse edge list (u, v, w + its CSR slot pair) written."""
+    return m * (4 + 4 + 8) + n * 4 + mc * 16
+
+
+def loss_bytes(n, m, nc, mc, K, S):
+    """Spectral-mismatch loss (forward) and its adjoint (the extra of the
+    backward pass), algorithmic bytes: fine Rayleigh quotients (edge list and
+    block), aggregate means, S coarse sweeps over the parameter weights (CSR
+    slots: column, edge id, weight; row pointers, degrees; block read and
+    written), the coarse quotients; backward: the sweeps recomputed with their
+    iterates saved, S adjoint sweeps, and the per-edge gradient reading each
+    saved iterate once."""
+    sweep = 2 * mc * 12 + 8 * (nc + 1) + 4 * nc + 2 * nc * K * 4
+    fwd = (m * 16 + 2 * n * K * 4) + (n * K * 4 + n * 4 + nc * K * 4) + S * sweep + (mc * 12 + nc * K * 4)
+    bwd = S * (sweep + 2 * nc * K * 4) + S * sweep + (mc * 12 + 3 * S * nc * K * 4)
+    return fwd, bwd
+
+
+def l2_copy_gbs(dev, mb=24, reps=200):
+    """Copy bandwidth of two L2-resident buffers (read + write bytes): the
+    yardstick for kernels whose working set lives in the 129 MB L2."""
+    import torch
+    a = torch.empty(mb * (1 << 20) // 4, dtype=torch.float32, device=dev).uniform_()
+    b = torch.empty_like(a)
+    for _ in range(10):
+        b.copy_(a)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        b.copy_(a)
+    e1.record()
+    torch.cuda.synchronize()
+    return 2.0 * a.numel() * 4 * reps / (e0.elapsed_time(e1) / 1000.0) / 1e9
 
 
 def kernel_source_sha(path):
@@ -177,9 +228,41 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # Oracle timing (CPU baseline / reference arm)
 # ---------------------------------------------------------------------------
+def cpu_info():
+    """Host CPU model and logical CPU count (the oracle runs on one of them)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for ln in f:
+                    if ln.lower().startswith(("model name", "cpu part")):
+                        model = ln.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    return {"cpu_model": model or platform.processor() or platform.machine(), "cpu_count": os.cpu_count(),
+            "machine": platform.machine()}
+
+
 def oracle_sample_graph(workload):
     import workloads as W
-    if workload == "chunglu_434k":
+    if workload == "knn_200k":
+        g = W.knn_gmm(200_000 // SAMPLE_DIV, 10, 10, 10, 12347)
+        desc = "kNN recipe at 1/%d of the points (%d points in 10-D, 10-component GMM, k=10, Gaussian weights)" % (
+            SAMPLE_DIV, g.n)
+    elif workload == "knn_1m":
+        g = W.knn_gmm(1_000_000 // SAMPLE_DIV, 16, 20, 15, 12350)
+        desc = "kNN recipe at 1/%d of the points (%d points in 16-D, 20-component GMM, k=15, Gaussian weights)" % (
+            SAMPLE_DIV, g.n)
+    elif workload == "chunglu_434k":
         g = W.chung_lu(434_000 // SAMPLE_DIV, 16_000_000 // SAMPLE_DIV)
         desc = "Chung-Lu recipe at 1/%d scale (%d nodes, %d edges, same mean degree and exponent)" % (
             SAMPLE_DIV, g.n, g.m)
@@ -190,8 +273,7 @@ def oracle_sample_graph(workload):
         g = W.grid2d(64, 64)
         desc = "the full 64x64 grid"
     else:
-        g = W.chung_lu(434_000 // SAMPLE_DIV, 16_000_000 // SAMPLE_DIV)
-        desc = "Chung-Lu recipe at 1/%d scale" % SAMPLE_DIV
+        raise ValueError("no oracle sample for workload %r" % workload)
     return g, desc
 
 
@@ -232,8 +314,9 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "sample": desc, "K": wl.K, "sweeps": wl.sweeps, "omega": wl.omega},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "FP64 C oracle, single thread, full level loop on " + desc},
+        "cpu_baseline": dict({"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                              "sample": "FP64 C oracle, single thread, full level loop on " + desc,
+                              "same_config": False}, **cpu_info()),
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -333,7 +416,7 @@ def main():
     lv0 = all_stats[-1][0]
     roofline = {
         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-        "peak_kind": peak_kind, "kernel": "k_sweep (weighted-Jacobi multi-vector SpMM)",
+        "peak_kind": peak_kind, "kernel": "k_sweep_row / k_sweep_stream (weighted-Jacobi multi-vector SpMM)",
         "bytes_per_launch_level0": sweep_bytes(lv0["n"], lv0["m"], wl.K, xbytes, wbytes),
         "traffic": traffic, "launches": sw_launches, "avg_launch_ms": sw_ms / max(sw_launches, 1),
     }
@@ -344,6 +427,41 @@ def main():
                           "t_smooth_ms": round(s["t_smooth"], 4), "t_affinity_ms": round(s["t_affinity"], 4),
                           "t_aggregate_ms": round(s["t_aggregate"], 4), "t_coarsen_ms": round(s["t_coarsen"], 4),
                           "edges_per_s": s["m"] / (t / 1000.0) if t > 0 else None})
+
+    # the other phases against the same HBM peak: algorithmic bytes (the
+    # helpers above) over each phase's event time (all its kernels and host
+    # synchronisations), summed over levels and steps
+    dbytes = 8 if wl.precision == "f64" else 4
+    acc = {"affinity": [0.0, 0.0], "aggregate": [0.0, 0.0], "coarsen": [0.0, 0.0]}
+    for stats in all_stats:
+        for s in stats:
+            acc["affinity"][0] += affinity_bytes(s["n"], s["m"], wl.K, xbytes, dbytes)
+            acc["affinity"][1] += s["t_affinity"]
+            acc["aggregate"][0] += aggregate_bytes(s["n"], s["m"], dbytes)
+            acc["aggregate"][1] += s["t_aggregate"]
+            acc["coarsen"][0] += galerkin_bytes(s["n"], s["m"], s["mc"])
+            acc["coarsen"][1] += s["t_coarsen"]
+    phases = {}
+    for k, (b, t) in acc.items():
+        gbs = b / (t / 1000.0) / 1e9 if t > 0 else 0.0
+        phases[k] = {"bytes_per_step": b / args.steps, "ms_per_step": t / args.steps, "achieved_gbs": gbs,
+                     "frac": gbs / peak, "unit": "GB/s", "bound": "hbm"}
+    roofline["phases"] = phases
+
+    # L2-side view of the sweep: every CSR slot gathers its neighbour's row,
+    # each row also reads itself and is written once, plus slots and row
+    # pointers; against the copy bandwidth of L2-resident buffers (the bound
+    # where the block lives in L2, as on the Chung-Lu graph)
+    if rank == 0:
+        l2peak = l2_copy_gbs(dev)
+        l2b = 0.0
+        for stats in all_stats:
+            for s in stats:
+                l2b += s["sweeps"] * ((2 * s["m"] + 2 * s["n"]) * wl.K * xbytes + 2 * s["m"] * (4 + wbytes)
+                                      + 8 * (s["n"] + 1))
+        l2a = l2b / (sw_ms / 1000.0) / 1e9 if sw_ms > 0 else 0.0
+        roofline["l2"] = {"achieved": l2a, "peak": l2peak, "unit": "GB/s", "frac": l2a / l2peak,
+                          "peak_kind": "measured: copy of two 24 MiB L2-resident buffers"}
 
     # end to end through the public API with host buffers
     e2e = None
@@ -370,9 +488,23 @@ def main():
         e2e = {"value": edges_per_step * k_e2e * world / te, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "steps": k_e2e}
 
+    # The oracle's level loop on the full configuration, once, outside the
+    # timed regions: the CPU baseline (one host core) and the reference the
+    # GPU paths' reduced graphs are checked against
+    orc = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle as _orc
+        _orc.build()
+        t0 = time.perf_counter()
+        orc_levels = _orc.reduce_multilevel(g.n, g.u, g.v, g.w, wl.K, wl.sweeps, wl.omega,
+                                            final_target=wl.final_target)
+        orc = (orc_levels, time.perf_counter() - t0)
+
     # FP32 (or BF16) path against the plain FP64 GPU path on the same graph:
-    # step-time speedup, and the 10 smallest nontrivial eigenvalues of the two
-    # final reduced graphs (FP64 solver on the host)
+    # step-time speedup; the 10 smallest nontrivial eigenvalues of each final
+    # reduced graph (FP64 solver on the host) against the oracle's reduced
+    # graph of the same configuration (the GPU FP64 graph when the oracle is
+    # skipped)
     cmp64 = None
     if rank == 0 and world == 1 and not args.no_fp64 and prec != gr.GR_F64:
         p64 = gr.ReduceParams(K=wl.K, sweeps=wl.sweeps, omega=wl.omega, seed=0, prec=gr.GR_F64, passes=2,
@@ -404,13 +536,28 @@ def main():
         for lv in (lv32, lv64):
             fu, fv, fw = (t.numpy() for t in gr.graph_reduce_get_edges(lv[-1], on_host=True))
             ev.append(_or.smallest_nontrivial_eigs(lv[-1].n, fu, fv, fw, 10))
-        rel = float(np.max(np.abs(ev[0] - ev[1]) / np.abs(ev[1])))
+        if orc is not None:
+            last = orc[0][-1]
+            ev_ref = _or.smallest_nontrivial_eigs(last.nc, last.uc, last.vc, last.wc, 10)
+            ref_kind = "oracle reduced graph (FP64 CPU level loop, same configuration)"
+        else:
+            ev_ref = ev[1]
+            ref_kind = "GPU FP64 reduced graph (oracle skipped)"
+        rel = float(np.max(np.abs(ev[0] - ev_ref) / np.abs(ev_ref)))
+        rel64 = float(np.max(np.abs(ev[1] - ev_ref) / np.abs(ev_ref)))
         same_maps = all(torch.equal(gr.graph_reduce_get_map(a), gr.graph_reduce_get_map(b))
                         for a, b in zip(lv32, lv64)) and len(lv32) == len(lv64)
         cmp64 = {"ms_per_step_fp64": t64, "ms_per_step": t_max / args.steps,
-                 "speedup": t64 / (t_max / args.steps), "lambda10_max_rel_err": rel,
-                 "at_accuracy": bool(rel <= 1e-3), "aggregates_identical": bool(same_maps),
-                 "lambda10_fp64": [float(x) for x in ev[1]]}
+                 "speedup": t64 / (t_max / args.steps), "lambda_reference": ref_kind,
+                 "lambda10_max_rel_err": rel, "at_accuracy": bool(rel <= 1e-3),
+                 "fp64_lambda10_max_rel_err": rel64,
+                 "fp32_vs_gpu_fp64_lambda10_max_rel_err": float(np.max(np.abs(ev[0] - ev[1]) / np.abs(ev[1]))),
+                 "aggregates_identical_fp32_fp64": bool(same_maps),
+                 "lambda10_reference": [float(x) for x in ev_ref]}
+        if orc is not None:
+            cmp64["fp64_maps_identical_to_oracle"] = bool(
+                len(orc[0]) == len(lv64)
+                and all(np.array_equal(gr.graph_reduce_get_map(b).cpu().numpy(), a.agg) for a, b in zip(orc[0], lv64)))
         # BF16 storage of the test vectors (FP32 accumulation), same comparison
         if prec != gr.GR_BF16:
             pb = gr.ReduceParams(K=wl.K, sweeps=wl.sweeps, omega=wl.omega, seed=0, prec=gr.GR_BF16, passes=2,
@@ -430,7 +577,7 @@ def main():
             tb = e0.elapsed_time(e1) / k64
             fu, fv, fw = (t.numpy() for t in gr.graph_reduce_get_edges(lvb[-1], on_host=True))
             evb = _or.smallest_nontrivial_eigs(lvb[-1].n, fu, fv, fw, 10)
-            relb = float(np.max(np.abs(evb - ev[1]) / np.abs(ev[1])))
+            relb = float(np.max(np.abs(evb - ev_ref) / np.abs(ev_ref)))
             m0 = gr.graph_reduce_get_map(lvb[0]).cpu().numpy()
             m64 = gr.graph_reduce_get_map(lv64[0]).cpu().numpy()
             cmp64["bf16_storage"] = {"ms_per_step": tb, "speedup_vs_fp64": t64 / tb, "lambda10_max_rel_err": relb,
@@ -514,8 +661,14 @@ def main():
 
         t_f, lval = tloss(False)
         t_fb, _ = tloss(True)
+        bf, bb = loss_bytes(g.n, g.m, Cl.n, Cl.m, wl.K, 5)
         lossm = {"fine_n": g.n, "coarse_n": Cl.n, "coarse_m": Cl.m, "K": wl.K, "coarse_sweeps": 5, "loss": lval,
-                 "ms_forward": t_f, "ms_forward_backward": t_fb}
+                 "ms_forward": t_f, "ms_forward_backward": t_fb,
+                 "bytes_forward": bf, "bytes_backward": bb,
+                 "achieved_gbs_forward": bf / (t_f / 1000.0) / 1e9,
+                 "achieved_gbs_forward_backward": (bf + bb) / (t_fb / 1000.0) / 1e9,
+                 "frac_forward": bf / (t_f / 1000.0) / 1e9 / peak,
+                 "frac_forward_backward": (bf + bb) / (t_fb / 1000.0) / 1e9 / peak}
 
         # Edge-weight scaling of the reduced graph (Alg. 1 driven by the loss
         # gradient): 10 iterations with eps = 0, eta_max sized so that the
@@ -603,11 +756,11 @@ def main():
         del Rd, Fd, lvd, Gd
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        gs, desc = oracle_sample_graph(args.workload)
-        e, dt, nl = time_oracle_multilevel(gs, wl)
-        cpu = {"value": e / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "FP64 C oracle, single thread, full level loop (%d levels) on %s, %.1f s" % (nl, desc, dt)}
+    if orc is not None:
+        e = sum(lv.m for lv in orc[0])
+        cpu = dict({"value": e / orc[1], "unit": UNIT, "cores": 1, "kind": "oracle", "same_config": True,
+                    "sample": "FP64 C oracle, one host core, one full step of this configuration (%d levels, "
+                              "%.1f s)" % (len(orc[0]), orc[1])}, **cpu_info())
 
     if rank == 0:
         line = {

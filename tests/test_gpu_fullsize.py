@@ -10,7 +10,8 @@ checked with what it can compute exactly:
   coarsen    the complete reduced graph from the GPU's map (pattern and
              weights bit-exact)
 and the level loop in FP64 is compared map by map with the oracle's own
-reduction of the 64^3 mesh, with the 10 eigenvalues of the final graphs.
+reduction of the 64^3 mesh, with the 10 eigenvalues of the final graphs (FP64
+and FP32 paths within 1e-3 of the oracle's reduced graph).
 """
 import numpy as np
 import pytest
@@ -94,8 +95,43 @@ def test_mesh64_levels_f64_against_oracle_reduction(gr, oracle_mod):
     last = levels[-1]
     ev_ref = oracle_mod.smallest_nontrivial_eigs(last.nc, last.uc, last.vc, last.wc, 10)
     assert np.max(np.abs(ev - ev_ref) / ev_ref) <= 1e-3
-    # the FP32 path on the same graph: eigenvalues reported against the oracle
+    # the FP32 path on the same graph: its final reduced graph's 10 smallest
+    # nontrivial eigenvalues within 1e-3 of the oracle's reduced graph
     g32, _ = gr.graph_reduce_multilevel(G, gr.ReduceParams(K=K, sweeps=S, prec=gr.GR_F32, final_target=final))
     u, v, w = (t.numpy() for t in gr.graph_reduce_get_edges(g32[-1], on_host=True))
     ev32 = oracle_mod.smallest_nontrivial_eigs(g32[-1].n, u, v, w, 10)
-    print("mesh64 FP32 path: 10-eigenvalue max rel err vs oracle %.3e" % np.max(np.abs(ev32 - ev_ref) / ev_ref))
+    err32 = np.max(np.abs(ev32 - ev_ref) / ev_ref)
+    assert err32 <= 1e-3, "mesh64 FP32 path: 10-eigenvalue max rel err vs oracle %.3e" % err32
+
+
+def test_chunglu_levels_against_oracle_reduction(gr, oracle_mod):
+    # The Chung-Lu recipe (degree exponent 2.5, mean degree 73.5) at 1/4 of
+    # the 434,000-node size: the coarse graphs stay dense, so the Galerkin
+    # product of every level takes the global-sort path.  FP64 maps bit-exact
+    # on every level against the oracle's own level loop; the 10 smallest
+    # nontrivial eigenvalues of the final graphs within 1e-3 of the oracle's
+    # for the FP64 and FP32 paths; BF16 storage reported.
+    g = W.chung_lu(108_500, 4_000_000, max_deg=600.0)
+    K, S, final = 16, 5, 3250
+    levels = oracle_mod.reduce_multilevel(g.n, g.u, g.v, g.w, K, S, final_target=final)
+    last = levels[-1]
+    ev_ref = oracle_mod.smallest_nontrivial_eigs(last.nc, last.uc, last.vc, last.wc, 10)
+    G = gr.graph_reduce_create(g.n, g.u, g.v, g.w)
+    g64, _ = gr.graph_reduce_multilevel(G, gr.ReduceParams(K=K, sweeps=S, prec=gr.GR_F64, final_target=final))
+    assert len(g64) == len(levels) >= 2
+    for lv, gl in zip(levels, g64):
+        assert np.array_equal(gr.graph_reduce_get_map(gl).cpu().numpy(), lv.agg)
+    u, v, w = (t.numpy() for t in gr.graph_reduce_get_edges(g64[-1], on_host=True))
+    assert np.array_equal(u, last.uc) and np.array_equal(v, last.vc)
+    assert np.max(np.abs(w - last.wc) / last.wc) <= 1e-6
+    ev64 = oracle_mod.smallest_nontrivial_eigs(g64[-1].n, u, v, w, 10)
+    assert np.max(np.abs(ev64 - ev_ref) / ev_ref) <= 1e-3
+    g32, _ = gr.graph_reduce_multilevel(G, gr.ReduceParams(K=K, sweeps=S, prec=gr.GR_F32, final_target=final))
+    u, v, w = (t.numpy() for t in gr.graph_reduce_get_edges(g32[-1], on_host=True))
+    ev32 = oracle_mod.smallest_nontrivial_eigs(g32[-1].n, u, v, w, 10)
+    err32 = np.max(np.abs(ev32 - ev_ref) / ev_ref)
+    assert err32 <= 1e-3, "chunglu FP32 path: 10-eigenvalue max rel err vs oracle %.3e" % err32
+    gb, _ = gr.graph_reduce_multilevel(G, gr.ReduceParams(K=K, sweeps=S, prec=gr.GR_BF16, final_target=final))
+    u, v, w = (t.numpy() for t in gr.graph_reduce_get_edges(gb[-1], on_host=True))
+    evb = oracle_mod.smallest_nontrivial_eigs(gb[-1].n, u, v, w, 10)
+    print("chunglu BF16 storage: 10-eigenvalue max rel err vs oracle %.3e" % np.max(np.abs(evb - ev_ref) / ev_ref))
