@@ -121,25 +121,6 @@ def loss_bytes(n, m, nc, mc, K, S):
     return fwd, bwd
 
 
-def l2_copy_gbs(dev, mb=24, reps=200):
-    """Copy bandwidth of two L2-resident buffers (read + write bytes): the
-    yardstick for kernels whose working set lives in the 129 MB L2."""
-    import torch
-    a = torch.empty(mb * (1 << 20) // 4, dtype=torch.float32, device=dev).uniform_()
-    b = torch.empty_like(a)
-    for _ in range(10):
-        b.copy_(a)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(reps):
-        b.copy_(a)
-    e1.record()
-    torch.cuda.synchronize()
-    return 2.0 * a.numel() * 4 * reps / (e0.elapsed_time(e1) / 1000.0) / 1e9
-
-
 def kernel_source_sha(path):
     import hashlib
     with open(path, "rb") as f:
@@ -447,21 +428,6 @@ def main():
         phases[k] = {"bytes_per_step": b / args.steps, "ms_per_step": t / args.steps, "achieved_gbs": gbs,
                      "frac": gbs / peak, "unit": "GB/s", "bound": "hbm"}
     roofline["phases"] = phases
-
-    # L2-side view of the sweep: every CSR slot gathers its neighbour's row,
-    # each row also reads itself and is written once, plus slots and row
-    # pointers; against the copy bandwidth of L2-resident buffers (the bound
-    # where the block lives in L2, as on the Chung-Lu graph)
-    if rank == 0:
-        l2peak = l2_copy_gbs(dev)
-        l2b = 0.0
-        for stats in all_stats:
-            for s in stats:
-                l2b += s["sweeps"] * ((2 * s["m"] + 2 * s["n"]) * wl.K * xbytes + 2 * s["m"] * (4 + wbytes)
-                                      + 8 * (s["n"] + 1))
-        l2a = l2b / (sw_ms / 1000.0) / 1e9 if sw_ms > 0 else 0.0
-        roofline["l2"] = {"achieved": l2a, "peak": l2peak, "unit": "GB/s", "frac": l2a / l2peak,
-                          "peak_kind": "measured: copy of two 24 MiB L2-resident buffers"}
 
     # end to end through the public API with host buffers
     e2e = None

@@ -494,7 +494,6 @@ __global__ void __launch_bounds__(SM_THREADS) k_sweep_row(
                         for (int e = 0; e < E; ++e) acc[e] = fma(w, x[u][e], acc[e]);
                     }
             }
-#ifndef GR_NO_SLOT_PF
             if (q == 0 && e1 > b1) {
                 // the next group's slot lines into L1 (its row pointers have
                 // arrived by now): its slot loads then wait on L1, not on
@@ -504,7 +503,6 @@ __global__ void __launch_bounds__(SM_THREADS) k_sweep_row(
                 asm volatile("prefetch.global.L1 [%0];" ::"l"(p0));
                 if (((uintptr_t)p0 >> 7) != ((uintptr_t)p1 >> 7)) asm volatile("prefetch.global.L1 [%0];" ::"l"(p1));
             }
-#endif
             if (row < n) {
                 const bool isolated = b0 == e0;
                 Acc y[E];
