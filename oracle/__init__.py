@@ -60,6 +60,7 @@ def _load():
         "oracle_coarsen": (I, [I64, I64, P, P, P, P, I64, P, P, P, P]),
         "oracle_loss": (I, [I64, I64, P, P, P, I64, I64, P, P, P, P, I, P, I, D, P, P, P, P]),
         "oracle_shifted_jacobi": (I, [I64, I64, P, P, P, I, P, I, D, I, P]),
+        "oracle_shifted_jacobi_mass": (I, [I64, I64, P, P, P, I, P, P, D, I, P]),
         "oracle_colour": (I, [I64, I64, P, P, U64, P, P]),
         "oracle_gs_sweeps": (I, [I64, I64, P, P, P, I, P, I, D, P]),
         "oracle_smooth_gs": (I, [I64, I64, P, P, P, I, I, D, U64, I, U64, P]),
@@ -367,21 +368,60 @@ def shifted_jacobi(n, u, v, w, Y, lam, normalized=False, omega=0.7, iters=10):
     return Y
 
 
-def coarsest_eigenpairs(n, u, v, w, k, normalized=False):
+def shifted_jacobi_mass(n, u, v, w, Y, lam, b, omega=0.7, iters=10):
+    """`iters` weighted-Jacobi iterations on (L - lam_k B) y = 0 with an
+    explicit diagonal mass B = diag(b) (oracle_shifted_jacobi_mass)."""
+    Y = np.array(Y, dtype=np.float64, order="C", copy=True)
+    K = Y.shape[1]
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    assert lam.shape == (K,) and b.shape == (n,)
+    lib = _load()
+    u, v, w = _i32(u), _i32(v), _f64(w)
+    _check(lib.oracle_shifted_jacobi_mass(n, len(u), _p(u), _p(v), _p(w), K, _p(lam), _p(b), float(omega),
+                                          int(iters), _p(Y)), "shifted_jacobi_mass")
+    return Y
+
+
+def coarsest_eigenpairs(n, u, v, w, k, normalized=False, mass=None):
     """First k eigenpairs (ascending) of L u = lam B u on the coarsest graph
-    (Alg. 5, step 2) by a dense symmetric eigensolver.  B = D is reduced to
-    the standard problem D^-1/2 L D^-1/2 z = lam z, u = D^-1/2 z; a node of
-    degree 0 takes B(i,i) = 1 there (the paper is silent)."""
+    (Alg. 5, step 2) by a dense symmetric eigensolver.  B = D (normalized) or
+    an explicit positive diagonal `mass` is reduced to the standard problem
+    B^-1/2 L B^-1/2 z = lam z, u = B^-1/2 z; a node of degree 0 takes
+    B(i,i) = 1 in the normalised problem (the paper is silent)."""
     L = dense_laplacian(n, u, v, w)
-    if normalized:
-        b = degrees(n, u, v, w).copy()
-        b[b <= 0.0] = 1.0
+    if mass is not None or normalized:
+        if mass is not None:
+            b = np.asarray(mass, np.float64)
+        else:
+            b = degrees(n, u, v, w).copy()
+            b[b <= 0.0] = 1.0
         s = 1.0 / np.sqrt(b)
         lam, Z = np.linalg.eigh(s[:, None] * L * s[None, :])
         U = s[:, None] * Z
     else:
         lam, U = np.linalg.eigh(L)
     return lam[:k].copy(), np.ascontiguousarray(U[:, :k])
+
+
+def galerkin_masses(graphs, maps, normalized=False):
+    """The Galerkin-consistent masses B_l = P_l^T B_(l-1) P_l of every level:
+    B_0 = I (ratio cut) or D (normalised cut; a degree-0 node takes 1) on the
+    finest graph, and each coarser diagonal entry the sum of its members'
+    entries, added in ascending member id (P_l^T B P_l is diagonal because
+    each row of P_l holds a single 1)."""
+    n0, u0, v0, w0 = graphs[0]
+    if normalized:
+        b = degrees(n0, u0, v0, w0).copy()
+        b[b <= 0.0] = 1.0
+    else:
+        b = np.ones(n0, np.float64)
+    out = [b]
+    for j, mp in enumerate(maps):
+        bc = np.zeros(graphs[j + 1][0], np.float64)
+        np.add.at(bc, np.asarray(mp, np.int64), out[-1])
+        out.append(bc)
+    return out
 
 
 def gram_schmidt(U):
@@ -394,19 +434,30 @@ def gram_schmidt(U):
     return U
 
 
-def multilevel_eigensolve(graphs, maps, k, normalized=False, omega=0.7, iters=10):
+def multilevel_eigensolve(graphs, maps, k, normalized=False, omega=0.7, iters=10, mass="level"):
     """Alg. 5.  graphs[0] is the finest graph (n, u, v, w) and graphs[l] the
     graph coarsened from graphs[l-1] with aggregate map maps[l-1] (length
     n_{l-1}).  Coarsest eigenpairs, then for each finer level: map the block
     with H = P (U_fine[i] = U_coarse[map[i]]) and smooth every column with
     the coarsest eigenvalue as shift; orthonormalise at the finest level.
+    mass = "level": every level's B is its own I or D (Alg. 5 as written);
+    mass = "galerkin": B_l = P_l^T B_(l-1) P_l from the finest I or D
+    (galerkin_masses), which makes the coarsest problem the Rayleigh-Ritz
+    projection of the finest one onto the piecewise-constant vectors.
     Returns (U, lam) with lam the coarsest eigenvalues."""
-    assert len(maps) == len(graphs) - 1
-    lam, U = coarsest_eigenpairs(*graphs[-1], k, normalized)
+    assert len(maps) == len(graphs) - 1 and mass in ("level", "galerkin")
+    if mass == "level":
+        lam, U = coarsest_eigenpairs(*graphs[-1], k, normalized)
+    else:
+        B = galerkin_masses(graphs, maps, normalized)
+        lam, U = coarsest_eigenpairs(*graphs[-1], k, mass=B[-1])
     for j in range(len(graphs) - 2, -1, -1):
         U = U[np.asarray(maps[j], np.int64)]
         n, u, v, w = graphs[j]
-        U = shifted_jacobi(n, u, v, w, U, lam, normalized, omega, iters)
+        if mass == "level":
+            U = shifted_jacobi(n, u, v, w, U, lam, normalized, omega, iters)
+        else:
+            U = shifted_jacobi_mass(n, u, v, w, U, lam, B[j], omega, iters)
     return gram_schmidt(U), lam
 
 

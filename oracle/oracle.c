@@ -567,6 +567,44 @@ int oracle_shifted_jacobi(int64_t n, int64_t m, const int32_t* u, const int32_t*
 }
 
 /* ------------------------------------------------------------------------ */
+/* The same smoothing for an explicit diagonal mass B = diag(b) (the          */
+/* Galerkin-consistent mass of a coarse level, B_c = P^T B P, is diagonal):   */
+/*   y <- (1 - theta) y + theta (D - lambda_k b)^-1 A y,                       */
+/* a row whose shifted diagonal is not positive keeping its value; neighbour  */
+/* sums in ascending edge id.                                                  */
+/* ------------------------------------------------------------------------ */
+int oracle_shifted_jacobi_mass(int64_t n, int64_t m, const int32_t* u, const int32_t* v, const double* w, int K,
+                               const double* lambda, const double* b, double omega, int iters, double* Y) {
+    double* deg = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double* acc = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1) * (size_t)K);
+    if (!deg || !acc) {
+        free(deg);
+        free(acc);
+        return OR_ENOMEM;
+    }
+    int st = oracle_degrees(n, m, u, v, w, deg);
+    for (int it = 0; st == OR_OK && it < iters; ++it) {
+        memset(acc, 0, sizeof(double) * (size_t)n * (size_t)K);
+        for (int64_t e = 0; e < m; ++e) {
+            int64_t p = u[e], q = v[e];
+            for (int k = 0; k < K; ++k) {
+                acc[p * K + k] += w[e] * Y[q * K + k];
+                acc[q * K + k] += w[e] * Y[p * K + k];
+            }
+        }
+        for (int64_t i = 0; i < n; ++i)
+            for (int k = 0; k < K; ++k) {
+                double diag = deg[i] - lambda[k] * b[i];
+                if (diag > 0.0)
+                    Y[i * K + k] = (1.0 - omega) * Y[i * K + k] + omega * (acc[i * K + k] / diag);
+            }
+    }
+    free(deg);
+    free(acc);
+    return st;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Multicolour Gauss-Seidel (the relaxation Sec. 3.2.1 names).  The paper     */
 /* gives no ordering; reading: a greedy colouring in descending priority,      */
 /* priority of node i = (output number c+1 of SplitMix64 seeded with `seed`,   */

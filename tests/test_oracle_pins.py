@@ -670,6 +670,92 @@ def test_multilevel_eigensolve_prolongation_and_refinement(oracle_mod):
     assert np.all(np.abs(rq1[1:] - exact[1:]) < np.abs(rq0[1:] - exact[1:]))
 
 
+def _two_level_random(oracle_mod, seed, n=90, m=260):
+    g = W.random_sparse(n, m, seed=seed)
+    levels = oracle_mod.reduce_multilevel(g.n, g.u, g.v, g.w, 8, 4, final_target=14)
+    assert len(levels) >= 2
+    graphs = [(g.n, g.u, g.v, g.w)] + [(lv.nc, lv.uc, lv.vc, lv.wc) for lv in levels]
+    maps = [lv.agg for lv in levels]
+    return g, graphs, maps
+
+
+@pytest.mark.parametrize("normalized", [False, True])
+def test_galerkin_mass_is_rayleigh_ritz(oracle_mod, normalized):
+    # With B_l = P^T B_(l-1) P the coarsest problem is the projection of the
+    # finest (L, B) onto the piecewise-constant vectors Q (Q = P_1 P_2 ...):
+    # its eigenvalues are those of (Q^T L Q, Q^T B Q), computed here by a dense
+    # generalised solver, independently of the level-by-level Galerkin
+    # products and mass sums.  The level's own mass fails the identity.
+    import scipy.linalg
+    g, graphs, maps = _two_level_random(oracle_mod, 41 + int(normalized))
+    n, nc = g.n, graphs[-1][0]
+    Q = np.zeros((n, nc))
+    Q[np.arange(n), _compose(maps)] = 1.0
+    L = oracle_mod.dense_laplacian(g.n, g.u, g.v, g.w)
+    b0 = oracle_mod.degrees(g.n, g.u, g.v, g.w) if normalized else np.ones(n)
+    ref = scipy.linalg.eigh(Q.T @ L @ Q, Q.T @ np.diag(b0) @ Q, eigvals_only=True)[:6]
+    _, lam = oracle_mod.multilevel_eigensolve(graphs, maps, 6, normalized, iters=0, mass="galerkin")
+    assert np.allclose(lam, ref, rtol=1e-10, atol=1e-12)
+    _, lam_level = oracle_mod.multilevel_eigensolve(graphs, maps, 6, normalized, iters=0, mass="level")
+    assert not np.allclose(lam_level, ref, rtol=1e-3, atol=1e-6)
+    # Courant-Fischer: each is an upper bound of the finest generalised eigenvalue
+    fine = scipy.linalg.eigh(L, np.diag(b0), eigvals_only=True)[:6]
+    assert np.all(lam >= fine - 1e-10)
+
+
+def _compose(maps):
+    out = np.asarray(maps[0], np.int64)
+    for mp in maps[1:]:
+        out = np.asarray(mp, np.int64)[out]
+    return out
+
+
+def test_galerkin_mass_path_pairs_closed_form(oracle_mod):
+    # path of 64 unit edges, pairs (2i, 2i+1) aggregated: the coarse graph is
+    # the path of 32 unit edges with mass 2 on every node, so its eigenvalues
+    # are 4 sin^2(pi j / 64) / 2
+    n = 64
+    p = W.path(n)
+    agg = (np.arange(n) // 2).astype(np.int32)
+    uc, vc, wc = oracle_mod.coarsen(p.n, p.u, p.v, p.w, agg, n // 2)
+    graphs = [(p.n, p.u, p.v, p.w), (n // 2, uc, vc, wc)]
+    B = oracle_mod.galerkin_masses(graphs, [agg])
+    assert np.array_equal(B[1], np.full(n // 2, 2.0))
+    _, lam = oracle_mod.multilevel_eigensolve(graphs, [agg], 6, iters=0, mass="galerkin")
+    j = np.arange(6)
+    assert np.allclose(lam, 2.0 * np.sin(np.pi * j / n) ** 2, rtol=0, atol=1e-12)
+
+
+def test_galerkin_masses_are_member_sums(oracle_mod):
+    g, graphs, maps = _two_level_random(oracle_mod, 43)
+    for normalized in (False, True):
+        B = oracle_mod.galerkin_masses(graphs, maps, normalized)
+        b0 = oracle_mod.degrees(g.n, g.u, g.v, g.w) if normalized else np.ones(g.n)
+        comp = _compose(maps)
+        direct = np.zeros(graphs[-1][0])
+        np.add.at(direct, comp, b0)
+        assert np.allclose(B[-1], direct, rtol=1e-14, atol=0)
+        assert abs(B[-1].sum() - b0.sum()) <= 1e-12 * b0.sum()
+
+
+def test_shifted_jacobi_mass_fixed_point(oracle_mod):
+    # eigenpairs of (L, diag(b)) for a random positive b are fixed points of the
+    # explicit-mass iteration; with the wrong mass (b = 1) they move
+    import scipy.linalg
+    g = W.random_sparse(50, 140, seed=44)
+    rng = np.random.default_rng(5)
+    b = rng.uniform(0.5, 3.0, g.n)
+    L = oracle_mod.dense_laplacian(g.n, g.u, g.v, g.w)
+    lam, U = scipy.linalg.eigh(L, np.diag(b))
+    lam, U = lam[:4], U[:, :4]
+    Y = oracle_mod.shifted_jacobi_mass(g.n, g.u, g.v, g.w, U, lam, b, 0.7, 5)
+    deg = oracle_mod.degrees(g.n, g.u, g.v, g.w)
+    keep = np.all(deg[:, None] - lam[None, :] * b[:, None] > 0, axis=1)
+    assert np.allclose(Y[keep], U[keep], rtol=0, atol=1e-10)
+    Yw = oracle_mod.shifted_jacobi_mass(g.n, g.u, g.v, g.w, U, lam, np.ones(g.n), 0.7, 5)
+    assert not np.allclose(Yw[:, 1:], U[:, 1:], rtol=0, atol=1e-6)
+
+
 # ---------------------------------------------------------------------------
 # Reduced data set (Alg. 6, step 4): F_R = P^T F
 # ---------------------------------------------------------------------------
