@@ -593,7 +593,20 @@ def main():
                "smoothing_roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
                                       "frac": ach / peak, "bytes": sm_bytes},
                "lambda_coarsest": [float(x) for x in lam], "rayleigh": [float(x) for x in rq]}
-        del U, hier, lve, Ge
+        # the same with the Galerkin-consistent mass B_l = P^T B_(l-1) P: the
+        # coarsest eigenvalues are then Rayleigh-Ritz values of the finest
+        # problem (upper bounds of its eigenvalues), and the returned Rayleigh
+        # quotients show how close the refined vectors come to its low spectrum
+        gr.graph_reduce_eigensolve(hier, keig, False, 0.7, iters, want_rayleigh=False, galerkin_mass=True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        Ug, lamg, rqg = gr.graph_reduce_eigensolve(hier, keig, False, 0.7, iters, galerkin_mass=True)
+        e1.record()
+        torch.cuda.synchronize()
+        eig["galerkin_mass"] = {"ms": e0.elapsed_time(e1), "lambda_coarsest": [float(x) for x in lamg],
+                                "rayleigh": [float(x) for x in rqg]}
+        del U, Ug, hier, lve, Ge
 
     # Spectral-mismatch loss and its adjoint (the differentiable edge-weight
     # objective): fine graph against the final reduced graph through the

@@ -226,8 +226,14 @@ gr_status graph_reduce_reduce_data(gr_ctx* const* levels, int nlevels, const voi
 
 /* Multilevel Laplacian eigensolver (Alg. 5, Sec. 4.1; Eqs. equ:lgl and
  * equ:lgs).  The first k eigenpairs of L u = lambda B u on the coarsest level
- * (B = I for ratio cut, B = D for normalised cut) come from a dense FP64
- * symmetric eigensolver; then, level by level toward the finest, the block is
+ * come from a dense FP64 symmetric eigensolver; B is, on every level, either
+ * that level's own I (ratio cut) or D (normalised cut), as Alg. 5 states, or
+ * -- galerkin_mass = 1 -- the Galerkin-consistent mass B_l = P^T B_(l-1) P
+ * carried from the finest level's I or D (diagonal: each coarse entry the sum
+ * of its members', added in ascending member id), which makes the coarsest
+ * problem the projection of the finest one onto the piecewise-constant
+ * vectors (the paper does not say which; see Table "symbol" for P).  Then,
+ * level by level toward the finest, the block is
  * mapped with H = P (U_fine[i] = U_coarse[map[i]]) and every column k is
  * smoothed by `iters` weighted-Jacobi iterations on (L - lambda_k B) y = 0,
  *   y <- (1 - omega) y + omega (D - lambda_k B)^-1 A y,
@@ -238,14 +244,15 @@ gr_status graph_reduce_reduce_data(gr_ctx* const* levels, int nlevels, const voi
  *                 (l >= 1) coarsened from levels[l-1] (its parent map is H)
  *   k             1..32, at most the coarsest size (which must be <= 16384)
  *   normalized    0: B = I, 1: B = D (a degree-0 node takes B = 1 on the
- *                 coarsest level)
+ *                 coarsest level, and in the finest mass of galerkin_mass)
+ *   galerkin_mass 0: each level's own B; 1: B_l = P^T B_(l-1) P
  *   omega, iters  Jacobi weight (0, 1] and iterations per finer level
  *   U_out         device, n_0 x k row-major FP64, on levels[0]'s stream
  *   lambda_out    host, k FP64: the coarsest eigenvalues, ascending
  *   rayleigh_out  host, k FP64: x'Lx / x'Bx of the returned columns, or NULL
  * GR_EINVAL for a bad hierarchy or sizes; GR_ECUDA if the dense solver fails. */
-gr_status graph_reduce_eigensolve(gr_ctx* const* levels, int nlevels, int k, int normalized, double omega,
-                                  int iters, double* U_out, double* lambda_out, double* rayleigh_out);
+gr_status graph_reduce_eigensolve(gr_ctx* const* levels, int nlevels, int k, int normalized, int galerkin_mass,
+                                  double omega, int iters, double* U_out, double* lambda_out, double* rayleigh_out);
 
 /* Parameters of the level loop. */
 typedef struct gr_params {

@@ -85,7 +85,7 @@ def load():
         "graph_reduce_multilevel": (I, [P, ctypes.POINTER(gr_params), PP, ctypes.POINTER(I),
                                         ctypes.POINTER(gr_level_stats)]),
         "graph_reduce_compose_maps": (I, [PP, I, P]),
-        "graph_reduce_eigensolve": (I, [PP, I, I, I, D, I, P, P, P]),
+        "graph_reduce_eigensolve": (I, [PP, I, I, I, I, D, I, P, P, P]),
         "graph_reduce_reduce_data": (I, [PP, I, P, I, I, I, P]),
         "graph_reduce_scale_edges": (I, [P, P, P, P, I, I, D, D, D, D, D, I, P, ctypes.POINTER(I32), P, P]),
         "graph_reduce_loss_fwd": (I, [P, P, P, P, I, P, I, D, P, P]),
@@ -327,16 +327,19 @@ def graph_reduce_multilevel(g: Graph, params: ReduceParams, want_stats=True):
     return levels, out
 
 
-def graph_reduce_eigensolve(levels, k, normalized=False, omega=0.7, iters=10, want_rayleigh=True):
+def graph_reduce_eigensolve(levels, k, normalized=False, omega=0.7, iters=10, want_rayleigh=True,
+                            galerkin_mass=False):
     """Multilevel Laplacian eigensolver (Alg. 5) over ``levels`` = [finest
-    Graph, its coarsening, ...].  Returns (U, lam, rayleigh): U an n_0 x k FP64
-    device tensor, lam the coarsest eigenvalues, rayleigh the Rayleigh
-    quotients of U's columns (numpy arrays)."""
+    Graph, its coarsening, ...]; galerkin_mass selects B_l = P^T B_(l-1) P over
+    each level's own B.  Returns (U, lam, rayleigh): U an n_0 x k FP64 device
+    tensor, lam the coarsest eigenvalues, rayleigh the Rayleigh quotients of
+    U's columns (numpy arrays)."""
     arr = (ctypes.c_void_p * len(levels))(*[lv.handle.value for lv in levels])
     U = torch.empty(levels[0].n, k, dtype=torch.float64, device=levels[0].device)
     lam = np.zeros(k, np.float64)
     rq = np.zeros(k, np.float64) if want_rayleigh else None
-    st = load().graph_reduce_eigensolve(arr, len(levels), int(k), 1 if normalized else 0, float(omega), int(iters),
+    st = load().graph_reduce_eigensolve(arr, len(levels), int(k), 1 if normalized else 0, 1 if galerkin_mass else 0,
+                                        float(omega), int(iters),
                                         _ptr(U), lam.ctypes.data_as(ctypes.c_void_p),
                                         rq.ctypes.data_as(ctypes.c_void_p) if rq is not None else None)
     _check(st, levels[0].handle)

@@ -246,13 +246,14 @@ gr_status graph_reduce_reduce_data(gr_ctx* const* levels, int nlevels, const voi
     return reduce_data_impl(levels, nlevels, F, d, f64, mean, F_out);
 }
 
-gr_status graph_reduce_eigensolve(gr_ctx* const* levels, int nlevels, int k, int normalized, double omega,
-                                  int iters, double* U_out, double* lambda_out, double* rayleigh_out) {
+gr_status graph_reduce_eigensolve(gr_ctx* const* levels, int nlevels, int k, int normalized, int galerkin_mass,
+                                  double omega, int iters, double* U_out, double* lambda_out, double* rayleigh_out) {
     if (!levels || nlevels < 1 || !levels[0]) return set_error(nullptr, GR_EINVAL, "eigensolve: no levels");
     gr_ctx* f = levels[0];
     if (!U_out || !lambda_out) return set_error(f, GR_EINVAL, "eigensolve: NULL output");
-    if (k < 1 || k > 32 || iters < 0 || !(omega > 0.0 && omega <= 1.0) || (normalized != 0 && normalized != 1))
-        return set_error(f, GR_EINVAL, "eigensolve: need 1 <= k <= 32, iters >= 0, 0 < omega <= 1");
+    if (k < 1 || k > 32 || iters < 0 || !(omega > 0.0 && omega <= 1.0) || (normalized != 0 && normalized != 1) ||
+        (galerkin_mass != 0 && galerkin_mass != 1))
+        return set_error(f, GR_EINVAL, "eigensolve: need 1 <= k <= 32, iters >= 0, 0 < omega <= 1, flags 0 or 1");
     for (int l = 1; l < nlevels; ++l) {
         if (!levels[l] || !levels[l]->parent_map || levels[l]->parent_n != levels[l - 1]->n)
             return set_error(f, GR_EINVAL, "eigensolve: each level must be coarsened from the one before");
@@ -260,7 +261,8 @@ gr_status graph_reduce_eigensolve(gr_ctx* const* levels, int nlevels, int k, int
     const int64_t nc = levels[nlevels - 1]->n;
     if (nc > 16384) return set_error(f, GR_EINVAL, "eigensolve: the coarsest level must have at most 16384 nodes");
     if (k > nc) return set_error(f, GR_EINVAL, "eigensolve: k exceeds the coarsest level's size");
-    return eigensolve_impl(levels, nlevels, k, normalized, omega, iters, U_out, lambda_out, rayleigh_out);
+    return eigensolve_impl(levels, nlevels, k, normalized, galerkin_mass, omega, iters, U_out, lambda_out,
+                           rayleigh_out);
 }
 
 gr_status graph_reduce_multilevel(gr_ctx* fine, const gr_params* p, gr_ctx** levels_out, int* nlevels_out,

@@ -1,14 +1,18 @@
 // Multilevel Laplacian eigensolver (Alg. 5, Sec. 4.1; Eqs. equ:lgl, equ:lgs).
 //
 // Coarsest level: the first k eigenpairs of L u = lambda B u (B = I ratio
-// cut, B = D normalised cut) from a dense symmetric eigensolver (cuSOLVER
-// syevdx for the k smallest; the coarsest graph is small).  Then, level by level toward the
+// cut, B = D normalised cut, each level's own; or the Galerkin-consistent
+// mass B_l = P^T B_(l-1) P carried from the finest I or D) from a dense
+// symmetric eigensolver (cuSOLVER syevdx for the k smallest; the coarsest
+// graph is small).  Then, level by level toward the
 // finest: U_fine = P U_coarse (the parent map), and `iters` weighted-Jacobi
 // iterations on (L - lambda_k B) y = 0 for every column k, the shift being the
 // coarsest eigenvalue.  Finally modified Gram-Schmidt over the columns.  Every
 // reduction is FP64 with a fixed summation order (per-block partials, then a
 // last-block finish), so results are reproducible.
 #include <cusolverDn.h>
+
+#include <vector>
 
 #include "gr_internal.cuh"
 
@@ -18,36 +22,34 @@ namespace {
 
 constexpr int ET = 256;
 
-// dense column-major L (or D^-1/2 L D^-1/2) of a small graph, thread per row
+// dense column-major L, or B^-1/2 L B^-1/2 for a diagonal mass b (b = NULL:
+// B = I; an entry that is not positive -- a degree-0 node under B = D --
+// counts as 1), of a small graph, thread per row
 __global__ void k_dense_laplacian(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                                   const int32_t* __restrict__ eid, const double* __restrict__ ew,
-                                  const double* __restrict__ deg, int normalized, double* __restrict__ A) {
+                                  const double* __restrict__ deg, const double* __restrict__ b,
+                                  double* __restrict__ A) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double bi = deg[i] > 0.0 ? deg[i] : 1.0;
-    const double si = normalized ? 1.0 / sqrt(bi) : 1.0;
+    auto inv_sqrt = [&](int64_t r) { return b ? 1.0 / sqrt(b[r] > 0.0 ? b[r] : 1.0) : 1.0; };
+    const double si = inv_sqrt(i);
     A[i + i * n] = si * deg[i] * si;
     for (int64_t j = rowptr[i]; j < rowptr[i + 1]; ++j) {
         const int64_t q = col[j];
-        const double bq = deg[q] > 0.0 ? deg[q] : 1.0;
-        const double sq = normalized ? 1.0 / sqrt(bq) : 1.0;
-        A[i + q * n] = si * (-ew[eid[j]]) * sq;
+        A[i + q * n] = si * (-ew[eid[j]]) * inv_sqrt(q);
     }
 }
 
 // first k eigenvectors (columns of the column-major A) into a row-major n x k
-// block, mapped back by D^-1/2 for the normalised problem
-__global__ void k_take_eigvecs(int64_t n, int k, const double* __restrict__ A, const double* __restrict__ deg,
-                               int normalized, double* __restrict__ U) {
+// block, mapped back by B^-1/2 for a diagonal mass b (NULL: B = I)
+__global__ void k_take_eigvecs(int64_t n, int k, const double* __restrict__ A, const double* __restrict__ b,
+                               double* __restrict__ U) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= n * k) return;
     const int64_t i = idx / k;
     const int c = (int)(idx % k);
     double x = A[i + (int64_t)c * n];
-    if (normalized) {
-        const double b = deg[i] > 0.0 ? deg[i] : 1.0;
-        x = x / sqrt(b);
-    }
+    if (b) x = x / sqrt(b[i] > 0.0 ? b[i] : 1.0);
     U[idx] = x;
 }
 
@@ -63,19 +65,21 @@ __global__ void k_prolong(int64_t n, int k, const int32_t* __restrict__ map, con
 
 // One weighted-Jacobi iteration on (L - lambda_c B) y = 0 for every column c,
 // thread per (row, column): y <- (1 - w) y + w (A y)_r / (D_r - lambda_c B_r),
-// with (A y)_r = D_r (D^-1 A y)_r from the row-scaled weights; a row whose
-// shifted diagonal is not positive keeps its value.
+// with (A y)_r = D_r (D^-1 A y)_r from the row-scaled weights and B the
+// diagonal mass b (NULL: B = I); a row whose shifted diagonal is not positive
+// keeps its value.
 __global__ void k_shifted_jacobi(int64_t n, int k, const int64_t* __restrict__ rowptr,
                                  const int32_t* __restrict__ col, const double* __restrict__ wn64,
-                                 const double* __restrict__ deg, const double* __restrict__ lam, int normalized,
-                                 double omega, const double* __restrict__ Yin, double* __restrict__ Yout) {
+                                 const double* __restrict__ deg, const double* __restrict__ lam,
+                                 const double* __restrict__ b, double omega, const double* __restrict__ Yin,
+                                 double* __restrict__ Yout) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= n * k) return;
     const int64_t r = idx / k;
     const int c = (int)(idx % k);
     const double y = Yin[idx];
     const double D = deg[r];
-    const double diag = D - lam[c] * (normalized ? D : 1.0);
+    const double diag = D - lam[c] * (b ? b[r] : 1.0);
     if (!(diag > 0.0)) {
         Yout[idx] = y;
         return;
@@ -93,8 +97,9 @@ __global__ void __launch_bounds__(ET) k_shifted_jacobi_rows(int64_t n64, const i
                                                            const int32_t* __restrict__ col,
                                                            const double* __restrict__ wn64,
                                                            const double* __restrict__ deg,
-                                                           const double* __restrict__ lam_in, int normalized,
-                                                           double omega, const double* __restrict__ Yin,
+                                                           const double* __restrict__ lam_in,
+                                                           const double* __restrict__ b, double omega,
+                                                           const double* __restrict__ Yin,
                                                            double* __restrict__ Yout) {
     constexpr int E = K >= 2 ? 2 : 1, G = K / E, RPW = 32 / G;
     __shared__ double lam[K];
@@ -131,14 +136,21 @@ __global__ void __launch_bounds__(ET) k_shifted_jacobi_rows(int64_t n64, const i
             }
         }
         const double D = deg[r];
+        const double br = b ? b[r] : 1.0;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             const int c = q * E + e;
             const double y = Yin[r * K + c];
-            const double diag = D - lam[c] * (normalized ? D : 1.0);
+            const double diag = D - lam[c] * br;
             Yout[r * K + c] = diag > 0.0 ? (1.0 - omega) * y + omega * (acc[e] * D / diag) : y;
         }
     }
+}
+
+// finest-level mass: 1 (ratio cut) or the degree, 1 for a degree-0 node
+__global__ void k_base_mass(int64_t n, const double* __restrict__ deg, int normalized, double* __restrict__ b) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = normalized ? (deg[i] > 0.0 ? deg[i] : 1.0) : 1.0;
 }
 
 // row-major n x k <-> column-major
@@ -238,8 +250,8 @@ __global__ void k_scale_by(int64_t n, const double* __restrict__ x, const double
 
 }  // namespace
 
-gr_status eigensolve_impl(gr_ctx* const* levels, int nlevels, int k, int normalized, double omega, int iters,
-                          double* U_out, double* lambda_out, double* rayleigh_out) {
+gr_status eigensolve_impl(gr_ctx* const* levels, int nlevels, int k, int normalized, int galerkin_mass,
+                          double omega, int iters, double* U_out, double* lambda_out, double* rayleigh_out) {
     gr_ctx* f = levels[0];
     gr_ctx* c = levels[nlevels - 1];
     cudaStream_t s = f->stream;
@@ -262,6 +274,11 @@ gr_status eigensolve_impl(gr_ctx* const* levels, int nlevels, int k, int normali
                  o_V = add(sizeof(double) * (size_t)n0 * k), o_T = add(sizeof(double) * (size_t)n0),
                  o_part = add(sizeof(double) * (size_t)RB), o_sc = add(sizeof(double) * 64),
                  o_lam = add(sizeof(double) * 32), o_ctr = add(64), o_info = add(64);
+    // Galerkin masses of every level: b_0 = 1 or D (degree 0 -> 1), then the
+    // member sums level by level
+    std::vector<size_t> o_mass;
+    if (galerkin_mass)
+        for (int l = 0; l < nlevels; ++l) o_mass.push_back(add(sizeof(double) * (size_t)(levels[l]->n > 0 ? levels[l]->n : 1)));
     void* base;
     GR_TRY_CUDA(f, f->ws.get(WS_EIG, need, &base), "eigensolver scratch");
     char* Bp = (char*)base;
@@ -276,10 +293,27 @@ gr_status eigensolve_impl(gr_ctx* const* levels, int nlevels, int k, int normali
     unsigned* ctr = (unsigned*)(Bp + o_ctr);
     int* info = (int*)(Bp + o_info);
     GR_TRY_CUDA(f, cudaMemsetAsync(ctr, 0, 64, s), "memset");
+    // the diagonal mass of each level (NULL: B = I)
+    std::vector<const double*> mass(nlevels, nullptr);
+    if (galerkin_mass) {
+        double* b0 = (double*)(Bp + o_mass[0]);
+        k_base_mass<<<blocks(n0), ET, 0, s>>>(n0, f->deg, normalized, b0);
+        count_launch();
+        mass[0] = b0;
+        for (int l = 1; l < nlevels; ++l) {
+            double* bl = (double*)(Bp + o_mass[l]);
+            gr_ctx* const one[1] = {levels[l]};
+            const gr_status st = reduce_data_impl(one, 1, mass[l - 1], 1, 1, 0, bl);
+            if (st != GR_OK) return set_error(f, st, "eigensolve: Galerkin mass: " + levels[l]->last_error);
+            mass[l] = bl;
+        }
+    } else if (normalized) {
+        for (int l = 0; l < nlevels; ++l) mass[l] = levels[l]->deg;
+    }
 
     // 1) coarsest eigenpairs (Alg. 5 step 2, Eq. equ:lgs)
     GR_TRY_CUDA(f, cudaMemsetAsync(A, 0, sizeof(double) * (size_t)nc * (size_t)nc, s), "memset");
-    k_dense_laplacian<<<blocks(nc), ET, 0, s>>>(nc, c->rowptr, c->col, c->eid, c->ew, c->deg, normalized, A);
+    k_dense_laplacian<<<blocks(nc), ET, 0, s>>>(nc, c->rowptr, c->col, c->eid, c->ew, c->deg, mass[nlevels - 1], A);
     count_launch();
     // one solver handle per host thread and device, kept for later calls
     static thread_local cusolverDnHandle_t h = nullptr;
@@ -315,7 +349,7 @@ gr_status eigensolve_impl(gr_ctx* const* levels, int nlevels, int k, int normali
     if (((int*)hs)[0] != 0 || meig < k)
         return set_error(f, GR_ECUDA, "eigensolve: the dense eigensolver did not converge");
     int cur = 0;
-    k_take_eigvecs<<<blocks(nc * k), ET, 0, s>>>(nc, k, A, c->deg, normalized, Y[cur]);
+    k_take_eigvecs<<<blocks(nc * k), ET, 0, s>>>(nc, k, A, mass[nlevels - 1], Y[cur]);
     count_launch();
 
     // 2) map and smooth, level by level (Alg. 5 steps 4-10)
@@ -327,8 +361,8 @@ gr_status eigensolve_impl(gr_ctx* const* levels, int nlevels, int k, int normali
         cur ^= 1;
         for (int it = 0; it < iters; ++it) {
             const unsigned gr = (unsigned)(f->num_sms * 8);
-#define GR_SJ_ROWS(KK)                                                                                         \
-    k_shifted_jacobi_rows<KK><<<gr, ET, 0, s>>>(n, g->rowptr, g->col, g->wn64, g->deg, lam, normalized, omega, \
+#define GR_SJ_ROWS(KK)                                                                                      \
+    k_shifted_jacobi_rows<KK><<<gr, ET, 0, s>>>(n, g->rowptr, g->col, g->wn64, g->deg, lam, mass[l], omega, \
                                                 Y[cur], Y[cur ^ 1])
             switch (k) {
                 case 2: GR_SJ_ROWS(2); break;
@@ -338,7 +372,7 @@ gr_status eigensolve_impl(gr_ctx* const* levels, int nlevels, int k, int normali
                 case 32: GR_SJ_ROWS(32); break;
                 default:
                     k_shifted_jacobi<<<blocks(n * k), ET, 0, s>>>(n, k, g->rowptr, g->col, g->wn64, g->deg, lam,
-                                                                normalized, omega, Y[cur], Y[cur ^ 1]);
+                                                                mass[l], omega, Y[cur], Y[cur ^ 1]);
             }
 #undef GR_SJ_ROWS
             count_launch();

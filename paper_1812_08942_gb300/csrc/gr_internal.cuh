@@ -181,8 +181,8 @@ gr_status coarsen_impl(gr_ctx* c, const int32_t* agg, int64_t nc, gr_ctx** out);
 gr_status compose_impl(gr_ctx* const* levels, int nlevels, int32_t* out);
 gr_status reduce_data_impl(gr_ctx* const* levels, int nlevels, const void* F, int d, int f64, int mean,
                            void* F_out);
-gr_status eigensolve_impl(gr_ctx* const* levels, int nlevels, int k, int normalized, double omega, int iters,
-                          double* U_out, double* lambda_out, double* rayleigh_out);
+gr_status eigensolve_impl(gr_ctx* const* levels, int nlevels, int k, int normalized, int galerkin_mass,
+                          double omega, int iters, double* U_out, double* lambda_out, double* rayleigh_out);
 gr_status scale_edges_impl(gr_ctx* fine, gr_ctx* coarse, const int32_t* agg, const float* X, int K, int sweeps,
                            double omega, double alpha, double eta_max, double delta_bar, double eps, int kmax,
                            float* w, int32_t* iters_out, double* loss_hist, double* lam1_hist);

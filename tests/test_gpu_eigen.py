@@ -6,7 +6,9 @@ sides solve the same problem and no oracle input comes from the CUDA path.
 Eigenvectors are compared up to the sign of each column (a dense eigensolver
 fixes none); the graphs are connected and have random weights, so the
 eigenvalues are simple.  k = 2, 4, 8, 16, 32 take the row-chunk smoothing
-kernel, other k the thread-per-entry one.
+kernel, other k the thread-per-entry one.  Every case runs with each level's
+own mass B (Alg. 5 as written) and with the Galerkin-consistent mass
+B_l = P^T B_(l-1) P.
 """
 import numpy as np
 import pytest
@@ -56,15 +58,17 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("galerkin_mass", [False, True], ids=["level_mass", "galerkin_mass"])
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
-def test_eigensolve_parity(gr, oracle_mod, case):
+def test_eigensolve_parity(gr, oracle_mod, case, galerkin_mass):
     _, make, final, normalized, k, iters = case
     g = make()
     assert oracle_mod.n_components(g.n, g.u, g.v) == 1  # else lambda = 0 repeats and bases differ
     graphs, maps, ctxs = _hierarchy(gr, oracle_mod, g, final)
     assert len(ctxs) >= 3
-    Ur, lam_r = oracle_mod.multilevel_eigensolve(graphs, maps, k, normalized, 0.7, iters)
-    U, lam, rq = gr.graph_reduce_eigensolve(ctxs, k, normalized, 0.7, iters)
+    Ur, lam_r = oracle_mod.multilevel_eigensolve(graphs, maps, k, normalized, 0.7, iters,
+                                                 mass="galerkin" if galerkin_mass else "level")
+    U, lam, rq = gr.graph_reduce_eigensolve(ctxs, k, normalized, 0.7, iters, galerkin_mass=galerkin_mass)
     assert np.allclose(lam, lam_r, rtol=1e-10, atol=1e-12)
     assert _compare(U, Ur, 1e-8)
     L = oracle_mod.sparse_laplacian(g.n, g.u, g.v, g.w)
