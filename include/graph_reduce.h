@@ -106,12 +106,15 @@ gr_status graph_reduce_test_vectors(gr_ctx* ctx, int K, uint64_t seed, int level
  * The caller passes the graph (ctx, created beforehand) and the output X, as
  * for graph_reduce_smooth.  The scratch -- the second n x K block, the column
  * statistics and per-block partial sums, and, when the context does not hold
- * them yet, the packed FP64 slots (16 bytes per CSR slot, FP64 blocks) and
- * the streaming kernel's row partition -- lives in one 32 MiB device array
+ * them yet, the packed FP64 slots (16 bytes per CSR slot, FP64 blocks), the
+ * streaming kernel's row partition and the band kernel's far runs (16 bytes
+ * per band) -- lives in one 32 MiB device array
  * inside the library, held by every GPU that loads it until the process
  * exits; what a call needs must fit, else GR_EINVAL (n*K*sizeof(element) plus
  * about 1 MiB of statistics, and the rest as said).  Nothing is cached from
- * the array into the context.  The first call on a device looks up that array's device address
+ * the array into the context; only the band kernel's locality profile (33
+ * counts in host memory, measured on its first use with a stream
+ * synchronisation) is kept there.  The first call on a device looks up that array's device address
  * (cudaGetSymbolAddress) and should come before any stream capture.  All
  * calls share the array and it keeps the last call's contents: calls that
  * overlap on the GPU (other streams, other contexts) race and corrupt each
@@ -121,8 +124,8 @@ gr_status graph_reduce_smooth_noalloc(gr_ctx* ctx, int K, int sweeps, double ome
                                       uint64_t seed, int level, gr_prec prec, void* X);
 
 /* Sweep kernel behind graph_reduce_smooth and graph_reduce_smooth_noalloc on
- * this context.  The paper has no counterpart: these are two implementations
- * of the same weighted-Jacobi sweep (Alg. 3), each adding a row's products in
+ * this context.  The paper has no counterpart: these are implementations of
+ * the same weighted-Jacobi sweep (Alg. 3), each adding a row's products in
  * slot order, so they agree within the rounding of the column statistics.
  *   GR_SWEEP_AUTO    (default) the streaming kernel when rows are long (a
  *                    warp's group of 32 / lanes-per-row rows would hold over
@@ -131,14 +134,22 @@ gr_status graph_reduce_smooth_noalloc(gr_ctx* ctx, int K, int sweeps, double ome
  *                    row, several rows per warp, rows grid-strided
  *   GR_SWEEP_STREAM  warp per row over a slot-balanced row partition, the
  *                    slots staged through shared memory
+ *   GR_SWEEP_BAND    bands of consecutive rows staged with bulk copies: the
+ *                    rows within a halo of the band through a ring buffer in
+ *                    shared memory, the band's far neighbours as two
+ *                    contiguous runs; for graphs in a banded order (meshes,
+ *                    grids).  The first use measures the graph's locality
+ *                    (one kernel and a stream synchronisation) and keeps the
+ *                    far runs (16 bytes per band) in the context.  Falls back
+ *                    to the row-group kernel where no band fits shared memory.
  * GR_EINVAL for any other value. */
-typedef enum { GR_SWEEP_AUTO = 0, GR_SWEEP_ROW = 1, GR_SWEEP_STREAM = 2 } gr_sweep_kernel;
+typedef enum { GR_SWEEP_AUTO = 0, GR_SWEEP_ROW = 1, GR_SWEEP_STREAM = 2, GR_SWEEP_BAND = 3 } gr_sweep_kernel;
 
 gr_status graph_reduce_set_sweep_kernel(gr_ctx* ctx, gr_sweep_kernel kind);
 
 /* The sweep kernel graph_reduce_smooth runs on this context for K and prec
  * (no counterpart in the paper; for tuning and tests).
- *   kernel_out   host: GR_SWEEP_ROW or GR_SWEEP_STREAM */
+ *   kernel_out   host: GR_SWEEP_ROW, GR_SWEEP_STREAM or GR_SWEEP_BAND */
 gr_status graph_reduce_sweep_plan(gr_ctx* ctx, int K, gr_prec prec, int32_t* kernel_out);
 
 /* Test-vector smoothing with the Gauss-Seidel relaxation Sec. 3.2.1 names,

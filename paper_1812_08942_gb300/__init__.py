@@ -5,7 +5,7 @@ Galerkin coarsening -- as hand-written CUDA behind the C ABI in
 include/graph_reduce.h, with a thin ctypes binding of the same names.
 """
 from .binding import (  # noqa: F401
-    GR_BF16, GR_EINVAL, GR_F32, GR_F64, GR_SWEEP_AUTO, GR_SWEEP_ROW, GR_SWEEP_STREAM,
+    GR_BF16, GR_EINVAL, GR_F32, GR_F64, GR_SWEEP_AUTO, GR_SWEEP_BAND, GR_SWEEP_ROW, GR_SWEEP_STREAM,
     Graph, GraphReduceError, ReduceParams, graph_reduce_affinity,
     graph_reduce_aggregate, graph_reduce_coarsen, graph_reduce_colour, graph_reduce_compose_maps, graph_reduce_create,
     graph_reduce_eigensolve, graph_reduce_get_edges, graph_reduce_get_map, graph_reduce_loss_bwd, graph_reduce_loss_fwd,

@@ -18,7 +18,7 @@ _lib = None
 
 GR_OK, GR_EINVAL, GR_ENOMEM, GR_ECUDA, GR_ETIMEOUT, GR_ESTATE = range(6)
 GR_F64, GR_F32, GR_BF16 = 0, 1, 2
-GR_SWEEP_AUTO, GR_SWEEP_ROW, GR_SWEEP_STREAM = range(3)
+GR_SWEEP_AUTO, GR_SWEEP_ROW, GR_SWEEP_STREAM, GR_SWEEP_BAND = range(4)
 _STATUS = {1: "GR_EINVAL", 2: "GR_ENOMEM", 3: "GR_ECUDA", 4: "GR_ETIMEOUT", 5: "GR_ESTATE"}
 
 EXPORTED = [
@@ -186,7 +186,7 @@ def graph_reduce_set_sweep_kernel(g: Graph, kind: int):
 
 
 def graph_reduce_sweep_plan(g: Graph, K: int, dtype) -> int:
-    """The sweep kernel (GR_SWEEP_ROW / GR_SWEEP_STREAM) smoothing runs for K and dtype."""
+    """The sweep kernel (GR_SWEEP_ROW / GR_SWEEP_STREAM / GR_SWEEP_BAND) smoothing runs for K and dtype."""
     kind = ctypes.c_int32()
     _check(load().graph_reduce_sweep_plan(g.handle, int(K), _prec_of(dtype), ctypes.byref(kind)), g.handle)
     return int(kind.value)

@@ -118,7 +118,7 @@ gr_status graph_reduce_get_info(const gr_ctx* ctx, int64_t* n_out, int64_t* m_ou
 
 gr_status graph_reduce_set_sweep_kernel(gr_ctx* ctx, gr_sweep_kernel kind) {
     if (!ctx) return set_error(nullptr, GR_EINVAL, "set_sweep_kernel: ctx is NULL");
-    if ((int)kind < (int)GR_SWEEP_AUTO || (int)kind > (int)GR_SWEEP_STREAM)
+    if ((int)kind < (int)GR_SWEEP_AUTO || (int)kind > (int)GR_SWEEP_BAND)
         return set_error(ctx, GR_EINVAL, "set_sweep_kernel: unknown kernel");
     ctx->sweep_kind = (int)kind;
     return GR_OK;
@@ -408,7 +408,7 @@ void graph_reduce_destroy(gr_ctx* c) {
     if (!c) return;
     cudaStream_t s = c->stream;
     void* ptrs[] = {c->eu, c->ev, c->ew, c->eptr, c->rowptr, c->col, c->eid, c->cw32, c->wn64, c->deg,
-                    c->parent_map, c->wpart, c->cw64, c->gs_order};
+                    c->parent_map, c->wpart, c->cw64, c->gs_order, c->band_runs, c->band_slots};
     for (void* p : ptrs)
         if (p) cudaFreeAsync(p, s);
     c->ws.release();

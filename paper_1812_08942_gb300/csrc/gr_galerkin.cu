@@ -389,7 +389,7 @@ gr_status galerkin_rows(gr_ctx* c, const int32_t* agg, int64_t nc, gr_ctx* cc, b
 
     // coarse row pointers and edge-id bases
     GR_TRY_CUDA(c, cudaMallocAsync(&cc->eptr, sizeof(int64_t) * R, s), "alloc eptr");
-    GR_TRY_CUDA(c, cudaMallocAsync(&cc->rowptr, sizeof(int64_t) * R, s), "alloc rowptr");
+    GR_TRY_CUDA(c, cudaMallocAsync(&cc->rowptr, sizeof(int64_t) * (R + CSR_PAD_ROWS), s), "alloc rowptr");
     GR_TRY_CUDA(c, cudaMemsetAsync(ucnt + nc, 0, sizeof(int64_t), s), "memset");
     GR_TRY_CUDA(c, cudaMemsetAsync(upcnt + nc, 0, sizeof(int64_t), s), "memset");
     GR_TRY_CUDA(c, scan_exclusive_i64(ucnt, cc->rowptr, (int64_t)R, c->ws, s), "scan rows");
@@ -400,7 +400,7 @@ gr_status galerkin_rows(gr_ctx* c, const int32_t* agg, int64_t nc, gr_ctx* cc, b
     const int64_t mc = hs[0];
     if (hs[1] != 2 * mc) return set_error(c, GR_ECUDA, "coarsen: coarse rows are not symmetric");
     cc->m = mc;
-    const size_t cs = (size_t)(2 * mc > 0 ? 2 * mc : 1), ce = (size_t)(mc > 0 ? mc : 1);
+    const size_t cs = (size_t)(2 * mc > 0 ? 2 * mc : 1) + CSR_PAD_SLOTS, ce = (size_t)(mc > 0 ? mc : 1);
     GR_TRY_CUDA(c, cudaMallocAsync(&cc->eu, sizeof(int32_t) * ce, s), "alloc");
     GR_TRY_CUDA(c, cudaMallocAsync(&cc->ev, sizeof(int32_t) * ce, s), "alloc");
     GR_TRY_CUDA(c, cudaMallocAsync(&cc->ew, sizeof(double) * ce, s), "alloc");

@@ -295,9 +295,9 @@ gr_status build_csr(gr_ctx* c, bool check, bool* invalid) {
     int64_t* hs = host_scratch();
     if (!hs) return set_error(c, GR_ENOMEM, "csr: pinned scratch unavailable");
     GR_TRY_CUDA(c, cudaMallocAsync(&c->eptr, sizeof(int64_t) * (n + 1), s), "alloc eptr");
-    GR_TRY_CUDA(c, cudaMallocAsync(&c->rowptr, sizeof(int64_t) * (n + 1), s), "alloc rowptr");
+    GR_TRY_CUDA(c, cudaMallocAsync(&c->rowptr, sizeof(int64_t) * (n + 1 + CSR_PAD_ROWS), s), "alloc rowptr");
     GR_TRY_CUDA(c, cudaMallocAsync(&c->deg, sizeof(double) * (n > 0 ? n : 1), s), "alloc deg");
-    size_t slots = (size_t)(2 * m > 0 ? 2 * m : 1);
+    size_t slots = (size_t)(2 * m > 0 ? 2 * m : 1) + CSR_PAD_SLOTS;
     GR_TRY_CUDA(c, cudaMallocAsync(&c->col, sizeof(int32_t) * slots, s), "alloc col");
     GR_TRY_CUDA(c, cudaMallocAsync(&c->eid, sizeof(int32_t) * slots, s), "alloc eid");
     GR_TRY_CUDA(c, cudaMallocAsync(&c->cw32, sizeof(int2) * slots, s), "alloc cw32");

@@ -24,6 +24,22 @@ namespace gr {
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// Allocated entries past the end of the CSR arrays (rowptr, and col / eid /
+// cw32 / wn64): the band sweep copies row pointers and slots in 16-byte units
+// and may read up to one row pointer and three slots past the last one in use.
+constexpr int64_t CSR_PAD_ROWS = 1;
+constexpr size_t CSR_PAD_SLOTS = 4;
+
+// Shape of the band sweep on one graph (gr_band.cu)
+struct BandPlan {
+    int R = 0, H = 0;       // rows per band, halo rows on each side of a band
+    int SC = 0, FC = 0;     // slot capacity of a stage, rows per far run held
+    int WR = 0;             // rows of the window ring
+    int nbands = 0, grid = 0;
+    int off_stage = 0, stage_bytes = 0, off_sw = 0;
+    size_t smem = 0;        // dynamic shared memory per block
+};
+
 // Grow-only device scratch, stream-ordered (cudaMallocAsync / cudaFreeAsync).
 struct Workspace {
     struct Slot {
@@ -75,6 +91,15 @@ struct gr_ctx {
     int4* cw64 = nullptr;       // 2m: (col, 0, w / deg_row as FP64), built on first FP64 sweep
     // sweep kernel selection (gr_sweep_kernel)
     int sweep_kind = GR_SWEEP_AUTO;
+    // locality profile for the band sweep: slots with |col - row| in
+    // (2^(b-1), 2^b] per bucket b (bucket 0: <= 1, 32: beyond), built on first use
+    unsigned long long loc_hist[33] = {};
+    bool loc_ready = false;
+    // band sweep tables for one plan (band size, halo, grid, FP64 or not):
+    // far runs and window ring positions per band, and the slots' shared rows
+    int4* band_runs = nullptr;
+    void* band_slots = nullptr;
+    int band_key_R = 0, band_key_H = 0, band_key_grid = 0, band_key_f64 = 0;
     // multicolour Gauss-Seidel ordering for one colouring seed, built on first use:
     // nodes in ascending (colour, id) and each colour's range in that list
     int32_t* gs_order = nullptr;
@@ -89,6 +114,23 @@ struct gr_ctx {
 };
 
 namespace gr {
+
+// band sweep (gr_band.cu).  ensure_locality fills the context's locality
+// profile (one kernel and a readback into host memory; 264 bytes of device
+// scratch).  band_usable: a band plan for (prec, K) fits shared memory; unless
+// forced, also that the halo catches at least half of the slots.
+// band_prepare: the plan's per-band far runs and per-slot shared rows (16 + 8
+// bytes per band, 8 bytes per slot, 4 for FP64 blocks), kept in the context,
+// or, when `fixed`, built in `scratch` (scratch_bytes) if the context holds
+// none for this plan (cudaErrorMemoryAllocation if they do not fit).
+// sweep_band launches one sweep (err: device word set to 1 if a wait ran out).
+cudaError_t ensure_locality(gr_ctx* c, void* scratch264);
+bool band_usable(const gr_ctx* c, int prec, int K, bool forced, BandPlan* bp);
+cudaError_t band_prepare(gr_ctx* c, const BandPlan& bp, bool f64, bool fixed, void* scratch, size_t scratch_bytes,
+                         const int4** runs_out, const void** slots_out);
+cudaError_t sweep_band(gr_ctx* c, int prec, int K, const BandPlan& bp, const int4* runs, const void* slots,
+                       const void* Ain, void* Aout, double omega, const double* st_in, double* part, int part_cap,
+                       unsigned* counter, double* st_out, int* err);
 
 // primitives (gr_prims.cu)
 cudaError_t scan_exclusive_i64(const int64_t* in, int64_t* out, int64_t count, Workspace& ws,

@@ -591,11 +591,14 @@ constexpr int prec_of() {
 
 // the kernel every sweep of one smoothing call runs, and its inputs
 struct SweepPlan {
-    int kind = GR_SWEEP_ROW;     // GR_SWEEP_ROW / GR_SWEEP_STREAM
+    int kind = GR_SWEEP_ROW;     // GR_SWEEP_ROW / GR_SWEEP_STREAM / GR_SWEEP_BAND
     const int4* cw64 = nullptr;  // FP64 slots of the row-group and streaming kernels
     const int32_t* wpart = nullptr;
     int grid = 0;
     size_t dyn = 0;
+    BandPlan band;               // band kernel: its shape, far runs and slot rows
+    const int4* runs = nullptr;
+    const void* bslots = nullptr;
 };
 
 // packed (column, 0, FP64 weight) slots
@@ -659,11 +662,37 @@ static cudaError_t prepare_stream(gr_ctx* c, SweepScratch& sc, int part_cap, Swe
     return cudaGetLastError();
 }
 
+// Band kernel when forced and a band fits shared memory.  `tmp` (at least 264
+// bytes of device memory the stream does not use yet) holds the locality
+// profile's counts on the first call.
+template <typename T, int K>
+static cudaError_t prepare_band(gr_ctx* c, SweepScratch& sc, void* tmp, SweepPlan* P, bool* ok) {
+    *ok = false;
+    GR_CUDA(ensure_locality(c, tmp));
+    if (!band_usable(c, prec_of<T>(), K, true, &P->band)) return cudaSuccess;
+    void* scr = nullptr;
+    size_t scr_bytes = 0;
+    if (sc.fixed()) {  // what the context does not hold is built in the rest of the fixed array
+        const size_t off = (sc.used + 255) & ~size_t(255);
+        scr_bytes = off < sc.bytes ? sc.bytes - off : 0;
+        scr = scr_bytes ? sc.take(scr_bytes) : nullptr;
+    }
+    GR_CUDA(band_prepare(c, P->band, sizeof(T) == 8, sc.fixed(), scr, scr_bytes, &P->runs, &P->bslots));
+    P->kind = GR_SWEEP_BAND;
+    *ok = true;
+    return cudaSuccess;
+}
+
 // Kernel choice: forced by graph_reduce_set_sweep_kernel, or rows long enough
 // to fill a warp -> streaming kernel, otherwise the row-group kernel.
 template <typename T, int K>
-static cudaError_t sweep_prepare(gr_ctx* c, SweepScratch& sc, int part_cap, SweepPlan* P) {
+static cudaError_t sweep_prepare(gr_ctx* c, SweepScratch& sc, int part_cap, void* tmp, SweepPlan* P) {
     const int want = c->sweep_kind;
+    if (want == GR_SWEEP_BAND) {
+        bool ok = false;
+        GR_CUDA((prepare_band<T, K>(c, sc, tmp, P, &ok)));
+        if (ok) return cudaSuccess;
+    }
     if (want == GR_SWEEP_STREAM || (want == GR_SWEEP_AUTO && stream_wide<T, K>(c))) {
         P->kind = GR_SWEEP_STREAM;
         return prepare_stream<T, K>(c, sc, part_cap, P);
@@ -706,6 +735,9 @@ static cudaError_t launch_sweep_row(gr_ctx* c, const SweepPlan& P, const T* Ain,
 template <typename T, int K>
 static cudaError_t launch_sweep(gr_ctx* c, const SweepPlan& P, const T* Ain, T* Aout, double omega,
                                 const double* st_in, double* part, int part_cap, unsigned* counter, double* st_out) {
+    if (P.kind == GR_SWEEP_BAND)  // the error word follows the counter
+        return sweep_band(c, prec_of<T>(), K, P.band, P.runs, P.bslots, Ain, Aout, omega, st_in, part, part_cap,
+                          counter, st_out, (int*)(counter + 1));
     if (P.kind == GR_SWEEP_STREAM) {
         const typename SlotOf<T>::type* slots;
         if constexpr (sizeof(T) == 8) slots = P.cw64;
@@ -719,8 +751,8 @@ static cudaError_t launch_sweep(gr_ctx* c, const SweepPlan& P, const T* Ain, T* 
     return launch_sweep_row<T, K>(c, P, Ain, Aout, omega, st_in, part, part_cap, counter, st_out);
 }
 
-// Bytes of the statistics region: two 2K-double statistics sets and the
-// last-block counter.
+// Bytes of the statistics region: two 2K-double statistics sets, the
+// last-block counter and the band kernel's error word.
 template <int K>
 constexpr size_t stats_bytes() {
     return sizeof(double) * 4 * K + 64;
@@ -738,10 +770,11 @@ static cudaError_t run_sweeps(gr_ctx* c, SweepScratch& sc, int sweeps, double om
     double* st0 = stats;
     double* st1 = st0 + 2 * K;
     unsigned* counter = (unsigned*)(st1 + 2 * K);
-    // the counter must start at zero: the region may hold an earlier call's values
-    GR_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned), s));
+    // counter and error word start at zero: the region may hold an earlier call's values
+    GR_CUDA(cudaMemsetAsync(counter, 0, 2 * sizeof(unsigned), s));
     SweepPlan P;
-    if (sweeps > 0) GR_CUDA((sweep_prepare<T, K>(c, sc, part_cap, &P)));
+    // the partials are free until k_init: scratch for the locality profile
+    if (sweeps > 0) GR_CUDA((sweep_prepare<T, K>(c, sc, part_cap, part, &P)));
     const int igrid = init_grid<T, K>(c, n);
     k_init<T, K><<<igrid, SM_THREADS, 0, s>>>(n, seed, (uint64_t)level, X, part, counter, st0); count_launch();
     GR_CUDA(cudaGetLastError());
@@ -854,10 +887,21 @@ gr_status smooth_impl(gr_ctx* c, int K, int sweeps, double omega, uint64_t seed,
     return GR_OK;
 }
 
-// The kernel choice of sweep_prepare, without launching or allocating.
+// The kernel choice of sweep_prepare, without launching a sweep (the band
+// kernel's locality profile is measured on first use).
 template <typename T, int K>
 static cudaError_t sweep_plan_typed(gr_ctx* c, int32_t* kind) {
     const int want = c->sweep_kind;
+    if (want == GR_SWEEP_BAND) {
+        void* tmp = nullptr;
+        GR_CUDA(c->ws.get(WS_SMOOTH_PART, sizeof(double) * 2 * K * (size_t)part_capacity(c), &tmp));
+        GR_CUDA(ensure_locality(c, tmp));
+        BandPlan bp;
+        if (band_usable(c, prec_of<T>(), K, true, &bp)) {
+            *kind = GR_SWEEP_BAND;
+            return cudaSuccess;
+        }
+    }
     *kind = (want == GR_SWEEP_STREAM || (want == GR_SWEEP_AUTO && stream_wide<T, K>(c))) ? GR_SWEEP_STREAM
                                                                                          : GR_SWEEP_ROW;
     return cudaSuccess;

@@ -5,11 +5,11 @@ pre-reserved budget, or another framework's allocator): instead of the
 context's workspace it uses one fixed 32 MiB device array inside the library.
 It runs graph_reduce_smooth's own launch sequence, so the check is bitwise:
 through the C ABI, two calls in a row give exactly the vectors
-graph_reduce_smooth gives, for FP64, FP32 and BF16 storage, both sweep kernels
+graph_reduce_smooth gives, for FP64, FP32 and BF16 storage, each sweep kernel
 and 0, 4 and 5 sweeps (an even count ends in place in X).  The first calls run
-on a fresh context, so the FP64 packed slots and the streaming kernel's row
-partition are built inside the fixed array; a block too large for the array
-is refused.  This file is named to be collected last.
+on a fresh context, so the FP64 packed slots, the streaming kernel's row
+partition and the band kernel's far runs are built inside the fixed array; a
+block too large for the array is refused.  This file is named to be collected last.
 """
 import numpy as np
 import pytest
@@ -31,7 +31,7 @@ def gr():
 
 
 @pytest.mark.parametrize("sweeps", [0, 4, 5])
-@pytest.mark.parametrize("kernel", ["ROW", "STREAM"])
+@pytest.mark.parametrize("kernel", ["ROW", "STREAM", "BAND"])
 @pytest.mark.parametrize("dtype,K", [(torch.float64, 8), (torch.float32, 16), (torch.float32, 24),
                                      (torch.bfloat16, 16)])
 def test_noalloc_equals_smooth_bitwise(gr, dtype, K, kernel, sweeps):
