@@ -121,6 +121,10 @@ def loss_bytes(n, m, nc, mc, K, S):
     return fwd, bwd
 
 
+SWEEP_KERNEL_NAMES = {1: "k_sweep_row", 2: "k_sweep_stream", 3: "k_sweep_band"}
+SWEEP_KERNEL_SOURCES = {"k_sweep_row": "gr_smooth.cu", "k_sweep_stream": "gr_smooth.cu", "k_sweep_band": "gr_band.cu"}
+
+
 def kernel_source_sha(path):
     import hashlib
     with open(path, "rb") as f:
@@ -333,6 +337,7 @@ def main():
     g = wl.make(device=dev)
     prec = {"f64": gr.GR_F64, "f32": gr.GR_F32, "bf16": gr.GR_BF16}[wl.precision]
     xbytes = {"f64": 8, "f32": 4, "bf16": 2}[wl.precision]
+    xdtype = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}[wl.precision]
     wbytes = 8 if wl.precision == "f64" else 4
     params = gr.ReduceParams(K=wl.K, sweeps=wl.sweeps, omega=wl.omega, seed=0, prec=prec, passes=2,
                              level_ratio=4, final_target=wl.final_target, max_levels=32)
@@ -365,9 +370,11 @@ def main():
     t_begin = time.perf_counter()
     ev0.record()
     all_stats = []
+    last = None
     for _ in range(args.steps):
         G, levels, stats = step()
         all_stats.append(stats)
+        last = (G, levels)
         del G, levels
     ev1.record()
     torch.cuda.synchronize()
@@ -381,6 +388,12 @@ def main():
     edges_per_step = sum(s["m"] for s in all_stats[-1])
     value = whole_job_value(edges_per_step, args.steps, world, t_max)
 
+    # the sweep kernel each level ran (the automatic choice, kept per context)
+    sweep_kernels = []
+    for ctx in [last[0]] + list(last[1][:-1]):
+        sweep_kernels.append(SWEEP_KERNEL_NAMES[gr.graph_reduce_sweep_plan(ctx, wl.K, xdtype)])
+    del last
+
     # roofline of the dominant kernel: the Jacobi sweep (bytes / event time)
     sw_bytes = 0.0
     sw_ms = 0.0
@@ -392,12 +405,15 @@ def main():
             sw_launches += s["sweeps"]
     peak, peak_kind = load_peaks()
     achieved = sw_bytes / (sw_ms / 1000.0) / 1e9 if sw_ms > 0 else 0.0
-    src_sha = kernel_source_sha(os.path.join(ROOT, "paper_1812_08942_gb300", "csrc", "gr_smooth.cu"))
+    src_sha = kernel_source_sha(os.path.join(ROOT, "paper_1812_08942_gb300", "csrc",
+                                             SWEEP_KERNEL_SOURCES[sweep_kernels[0]]))
     traffic = traffic_from_profile(args.workload, src_sha)
     lv0 = all_stats[-1][0]
     roofline = {
         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-        "peak_kind": peak_kind, "kernel": "k_sweep_row / k_sweep_stream (weighted-Jacobi multi-vector SpMM)",
+        "peak_kind": peak_kind,
+        "kernel": "%s (weighted-Jacobi multi-vector SpMM; per level: %s)" % (sweep_kernels[0],
+                                                                               ", ".join(sweep_kernels)),
         "bytes_per_launch_level0": sweep_bytes(lv0["n"], lv0["m"], wl.K, xbytes, wbytes),
         "traffic": traffic, "launches": sw_launches, "avg_launch_ms": sw_ms / max(sw_launches, 1),
     }

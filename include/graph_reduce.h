@@ -107,14 +107,15 @@ gr_status graph_reduce_test_vectors(gr_ctx* ctx, int K, uint64_t seed, int level
  * for graph_reduce_smooth.  The scratch -- the second n x K block, the column
  * statistics and per-block partial sums, and, when the context does not hold
  * them yet, the packed FP64 slots (16 bytes per CSR slot, FP64 blocks), the
- * streaming kernel's row partition and the band kernel's far runs (16 bytes
- * per band) -- lives in one 32 MiB device array
- * inside the library, held by every GPU that loads it until the process
- * exits; what a call needs must fit, else GR_EINVAL (n*K*sizeof(element) plus
- * about 1 MiB of statistics, and the rest as said).  Nothing is cached from
- * the array into the context; only the band kernel's locality profile (33
- * counts in host memory, measured on its first use with a stream
- * synchronisation) is kept there.  The first call on a device looks up that array's device address
+ * streaming kernel's row partition and the band kernel's tables (24 bytes per
+ * band plus 8 bytes per slot, 4 for FP64 blocks) -- lives in one 32 MiB
+ * device array inside the library, held by every GPU that loads it until the
+ * process exits; what a call needs must fit, else GR_EINVAL (n*K*sizeof
+ * (element) plus about 1 MiB of statistics, and the rest as said).  Nothing
+ * is cached from the array into the context; only the band kernel's locality
+ * profile (33 counts) and the automatic choice's verdict on it, host values
+ * measured with stream synchronisations on first use, are kept there.  The
+ * first call on a device looks up that array's device address
  * (cudaGetSymbolAddress) and should come before any stream capture.  All
  * calls share the array and it keeps the last call's contents: calls that
  * overlap on the GPU (other streams, other contexts) race and corrupt each
@@ -129,7 +130,13 @@ gr_status graph_reduce_smooth_noalloc(gr_ctx* ctx, int K, int sweeps, double ome
  * slot order, so they agree within the rounding of the column statistics.
  *   GR_SWEEP_AUTO    (default) the streaming kernel when rows are long (a
  *                    warp's group of 32 / lanes-per-row rows would hold over
- *                    128 slots), else the row-group kernel
+ *                    128 slots); else the band kernel when the graph is in a
+ *                    banded order: at least half of its slots within a halo
+ *                    of at most 1,024 rows that fits shared memory, and at
+ *                    least 95 % of the neighbours held in shared memory by
+ *                    the band tables (measured once per context and plan:
+ *                    two stream synchronisations; tables of a graph that
+ *                    fails are freed); else the row-group kernel
  *   GR_SWEEP_ROW     row-group kernel: one lane per 16-byte chunk of a vector
  *                    row, several rows per warp, rows grid-strided
  *   GR_SWEEP_STREAM  warp per row over a slot-balanced row partition, the
@@ -140,8 +147,9 @@ gr_status graph_reduce_smooth_noalloc(gr_ctx* ctx, int K, int sweeps, double ome
  *                    contiguous runs; for graphs in a banded order (meshes,
  *                    grids).  The first use measures the graph's locality
  *                    (one kernel and a stream synchronisation) and keeps the
- *                    far runs (16 bytes per band) in the context.  Falls back
- *                    to the row-group kernel where no band fits shared memory.
+ *                    band tables in the context (24 bytes per band, and per
+ *                    slot 8 bytes, 4 for FP64 blocks).  Falls back to the
+ *                    row-group kernel where no band fits shared memory.
  * GR_EINVAL for any other value. */
 typedef enum { GR_SWEEP_AUTO = 0, GR_SWEEP_ROW = 1, GR_SWEEP_STREAM = 2, GR_SWEEP_BAND = 3 } gr_sweep_kernel;
 

@@ -30,7 +30,6 @@
 
 #include <limits.h>
 
-
 #include "gr_internal.cuh"
 #include "gr_sweep.cuh"
 #include "gr_vec.cuh"
@@ -79,18 +78,6 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_
                  "l"(src), "r"(bytes), "r"(sm_addr(b))
                  : "memory");
 }
-// barrier of the consumer warps only (id 1); returns how many of them passed `fail`
-__device__ __forceinline__ int consumers_count(bool fail) {
-    int r;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %1, 0;\n\t"
-        "bar.red.popc.u32 %0, 1, %2, p;\n\t}\n"
-        : "=r"(r)
-        : "r"((unsigned)fail), "n"(BAND_CT)
-        : "memory");
-    return r;
-}
-
 // bounded wait for the phase of parity `par`; gives up when another thread
 // has given up (*abort) or after BAND_WAIT_CYCLES (then sets *abort)
 __device__ bool mbar_wait(uint64_t* b, uint32_t par, volatile int* abort) {
@@ -230,11 +217,13 @@ __global__ void k_band_layout(int n, int nbands, int grid, int R, int H, int WR,
 // position inside the band's window, else the row of the band's stage in the
 // far area (lo run, then hi run), else -(column + 1): read from global
 // memory.  FP32 / BF16 blocks get (row, weight bits) pairs, FP64 blocks the
-// rows alone (the weights stay in wn64).  Warp per band.
+// rows alone (the weights stay in wn64).  *nglobal counts the slots read
+// from global memory.  Warp per band.
 template <bool F64>
 __global__ void k_band_slots(int n, int nbands, int R, int H, int WR, int FC, const int64_t* __restrict__ rowptr,
                              const int32_t* __restrict__ col, const int2* __restrict__ cw32,
-                             const int4* __restrict__ runs, const int2* __restrict__ lay, void* __restrict__ out) {
+                             const int4* __restrict__ runs, const int2* __restrict__ lay, void* __restrict__ out,
+                             unsigned long long* __restrict__ nglobal) {
     const int lane = threadIdx.x & 31;
     const int b = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     if (b >= nbands) return;
@@ -244,6 +233,7 @@ __global__ void k_band_slots(int n, int nbands, int R, int H, int WR, int FC, co
     const int2 ly = lay[b];
     const int nlo = far_held(run.y, FC), nhi = far_held(run.w, FC);
     const int far0 = WR + ly.y * 2 * FC;
+    unsigned ng = 0;
     for (int64_t j = rowptr[r0] + lane; j < rowptr[r0 + nrows]; j += 32) {
         const int c = col[j];
         int u;
@@ -256,10 +246,14 @@ __global__ void k_band_slots(int n, int nbands, int R, int H, int WR, int FC, co
             u = far0 + FC + (c - run.z);
         } else {
             u = -(c + 1);
+            ++ng;
         }
         if constexpr (F64) reinterpret_cast<int32_t*>(out)[j] = u;
         else reinterpret_cast<int2*>(out)[j] = make_int2(u, cw32[j].y);
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ng += __shfl_xor_sync(0xffffffffu, ng, o);
+    if (lane == 0 && ng) atomicAdd(nglobal, (unsigned long long)ng);
 }
 
 // ---------------------------------------------------------------------------
@@ -506,19 +500,24 @@ __global__ void __launch_bounds__(BAND_THREADS, 1) k_sweep_band(const __grid_con
         bool ok = true;
         for (int k = 0; ok && k < nb; ++k) {
             const int st = k % BAND_NS;
+            // each warp goes at its own pace; a wait that gave up ends the
+            // whole warp's work (and, through the abort word, every warp's)
             const bool fail = !mbar_wait(&ld_bar[st], (k / BAND_NS) & 1, abortp);
-            if (consumers_count(fail) != 0) {
+            if (__any_sync(0xffffffffu, fail)) {
+                *abortp = 1;
                 ok = false;
                 break;
             }
             const BandMeta M = meta[st];
             const unsigned char* S = bsm + a.off_stage + st * a.stage_bytes;
-            const int64_t* rp = reinterpret_cast<const int64_t*>(S);
+            // the low words of the row pointers give the local slot range
+            const int* rp32 = reinterpret_cast<const int*>(S);
+            const int s0lo = (int)M.s0a;
             for (int lr0 = warp * RPW; lr0 < M.nrows; lr0 += BAND_CW * RPW) {
                 const int lr = lr0 + seg;
                 if (!lane_ok || lr >= M.nrows) continue;
                 const int r = M.r0 + lr;
-                const int jb = (int)(rp[lr] - M.s0a), je = (int)(rp[lr + 1] - M.s0a);
+                const int jb = rp32[2 * lr] - s0lo, je = rp32[2 * lr + 2] - s0lo;
                 const int jm = je < M.nsc ? je : M.nsc;  // slots from jm on are read from global memory
                 Acc acc[E];
 #pragma unroll
@@ -706,6 +705,15 @@ static bool band_plan(const gr_ctx* c, bool forced, BandPlan* bp) {
         }                                                           \
     } while (0)
 
+void band_release(gr_ctx* c) {
+    if (c->band_runs) cudaFreeAsync(c->band_runs, c->stream);
+    if (c->band_slots) cudaFreeAsync(c->band_slots, c->stream);
+    c->band_runs = nullptr;
+    c->band_slots = nullptr;
+    c->band_key_R = c->band_key_H = c->band_key_grid = c->band_key_f64 = 0;
+    c->band_nglobal = -1;
+}
+
 bool band_usable(const gr_ctx* c, int prec, int K, bool forced, BandPlan* bp) {
     GR_BAND_DISPATCH(band_plan, c, forced, bp);
     return false;
@@ -713,31 +721,41 @@ bool band_usable(const gr_ctx* c, int prec, int K, bool forced, BandPlan* bp) {
 
 // The plan's far runs and slot rows: in the context (built once per plan), or,
 // when `fixed` and the context holds none for this plan, rebuilt in `scratch`
-// on every call.
+// on every call.  With nglobal, also the number of slots read from global
+// memory (a readback and a stream synchronisation unless already known).
 cudaError_t band_prepare(gr_ctx* c, const BandPlan& bp, bool f64, bool fixed, void* scratch, size_t scratch_bytes,
-                         const int4** runs_out, const void** slots_out) {
+                         const int4** runs_out, const void** slots_out, int64_t* nglobal) {
+    const size_t nb = (size_t)bp.nbands;
+    const size_t b_runs = (sizeof(int4) * nb + 255) & ~size_t(255);
+    const size_t b_lay = (sizeof(int2) * nb + 255) & ~size_t(255);
+    const size_t b_cnt = 256;
     if (c->band_runs && c->band_key_R == bp.R && c->band_key_H == bp.H && c->band_key_grid == bp.grid &&
         c->band_key_f64 == (int)f64) {
         *runs_out = c->band_runs;
         *slots_out = c->band_slots;
+        if (nglobal) {
+            if (c->band_nglobal < 0) {
+                int64_t* hs = host_scratch();
+                if (!hs) return cudaErrorMemoryAllocation;
+                GR_CUDA(cudaMemcpyAsync(hs, (char*)c->band_runs + b_runs + b_lay, sizeof(int64_t),
+                                        cudaMemcpyDeviceToHost, c->stream));
+                GR_CUDA(cudaStreamSynchronize(c->stream));
+                c->band_nglobal = hs[0];
+            }
+            *nglobal = c->band_nglobal;
+        }
         return cudaSuccess;
     }
-    const size_t nb = (size_t)bp.nbands;
-    const size_t b_runs = (sizeof(int4) * nb + 255) & ~size_t(255);
-    const size_t b_lay = (sizeof(int2) * nb + 255) & ~size_t(255);
     const size_t b_slots = (f64 ? sizeof(int32_t) : sizeof(int2)) * ((size_t)(2 * c->m) + CSR_PAD_SLOTS);
     char* base = nullptr;
     void* slots = nullptr;
     if (fixed) {
-        if (!scratch || b_runs + b_lay + b_slots > scratch_bytes) return cudaErrorMemoryAllocation;
+        if (!scratch || b_runs + b_lay + b_cnt + b_slots > scratch_bytes) return cudaErrorMemoryAllocation;
         base = (char*)scratch;
-        slots = base + b_runs + b_lay;
+        slots = base + b_runs + b_lay + b_cnt;
     } else {
-        if (c->band_runs) GR_CUDA(cudaFreeAsync(c->band_runs, c->stream));
-        if (c->band_slots) GR_CUDA(cudaFreeAsync(c->band_slots, c->stream));
-        c->band_runs = nullptr;
-        c->band_slots = nullptr;
-        GR_CUDA(cudaMallocAsync((void**)&c->band_runs, b_runs + b_lay, c->stream));
+        band_release(c);
+        GR_CUDA(cudaMallocAsync((void**)&c->band_runs, b_runs + b_lay + b_cnt, c->stream));
         GR_CUDA(cudaMallocAsync(&c->band_slots, b_slots, c->stream));
         c->band_key_R = bp.R;
         c->band_key_H = bp.H;
@@ -748,6 +766,8 @@ cudaError_t band_prepare(gr_ctx* c, const BandPlan& bp, bool f64, bool fixed, vo
     }
     int4* runs = (int4*)base;
     int2* lay = (int2*)(base + b_runs);
+    unsigned long long* cnt = (unsigned long long*)(base + b_runs + b_lay);
+    GR_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), c->stream));
     const int n = (int)c->n;
     const unsigned wblocks = (unsigned)ceil_div((int64_t)bp.nbands * 32, 256);
     k_band_runs<<<wblocks, 256, 0, c->stream>>>(n, bp.nbands, bp.R, bp.H, c->rowptr, c->col, runs);
@@ -757,14 +777,23 @@ cudaError_t band_prepare(gr_ctx* c, const BandPlan& bp, bool f64, bool fixed, vo
     count_launch();
     if (f64)
         k_band_slots<true><<<wblocks, 256, 0, c->stream>>>(n, bp.nbands, bp.R, bp.H, bp.WR, bp.FC, c->rowptr,
-                                                           c->col, c->cw32, runs, lay, slots);
+                                                           c->col, c->cw32, runs, lay, slots, cnt);
     else
         k_band_slots<false><<<wblocks, 256, 0, c->stream>>>(n, bp.nbands, bp.R, bp.H, bp.WR, bp.FC, c->rowptr,
-                                                            c->col, c->cw32, runs, lay, slots);
+                                                            c->col, c->cw32, runs, lay, slots, cnt);
     count_launch();
+    GR_CUDA(cudaGetLastError());
     *runs_out = runs;
     *slots_out = slots;
-    return cudaGetLastError();
+    if (nglobal) {
+        int64_t* hs = host_scratch();
+        if (!hs) return cudaErrorMemoryAllocation;
+        GR_CUDA(cudaMemcpyAsync(hs, cnt, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
+        GR_CUDA(cudaStreamSynchronize(c->stream));
+        *nglobal = hs[0];
+        if (!fixed) c->band_nglobal = hs[0];
+    }
+    return cudaSuccess;
 }
 
 template <typename T, int K>

@@ -100,6 +100,10 @@ struct gr_ctx {
     int4* band_runs = nullptr;
     void* band_slots = nullptr;
     int band_key_R = 0, band_key_H = 0, band_key_grid = 0, band_key_f64 = 0;
+    int64_t band_nglobal = -1;  // slots of those tables read from global memory (-1: not read back)
+    // the automatic kernel choice's verdict on the band kernel for one plan
+    // (-1: not decided)
+    int band_auto_R = 0, band_auto_H = 0, band_auto_grid = 0, band_auto_f64 = 0, band_auto_ok = -1;
     // multicolour Gauss-Seidel ordering for one colouring seed, built on first use:
     // nodes in ascending (colour, id) and each colour's range in that list
     int32_t* gs_order = nullptr;
@@ -122,12 +126,15 @@ namespace gr {
 // band_prepare: the plan's per-band far runs and per-slot shared rows (16 + 8
 // bytes per band, 8 bytes per slot, 4 for FP64 blocks), kept in the context,
 // or, when `fixed`, built in `scratch` (scratch_bytes) if the context holds
-// none for this plan (cudaErrorMemoryAllocation if they do not fit).
+// none for this plan (cudaErrorMemoryAllocation if they do not fit); with
+// nglobal, the count of slots read from global memory (synchronises the
+// stream unless known).  band_release frees the context's tables.
 // sweep_band launches one sweep (err: device word set to 1 if a wait ran out).
 cudaError_t ensure_locality(gr_ctx* c, void* scratch264);
 bool band_usable(const gr_ctx* c, int prec, int K, bool forced, BandPlan* bp);
 cudaError_t band_prepare(gr_ctx* c, const BandPlan& bp, bool f64, bool fixed, void* scratch, size_t scratch_bytes,
-                         const int4** runs_out, const void** slots_out);
+                         const int4** runs_out, const void** slots_out, int64_t* nglobal);
+void band_release(gr_ctx* c);
 cudaError_t sweep_band(gr_ctx* c, int prec, int K, const BandPlan& bp, const int4* runs, const void* slots,
                        const void* Ain, void* Aout, double omega, const double* st_in, double* part, int part_cap,
                        unsigned* counter, double* st_out, int* err);

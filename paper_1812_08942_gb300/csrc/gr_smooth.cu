@@ -662,14 +662,27 @@ static cudaError_t prepare_stream(gr_ctx* c, SweepScratch& sc, int part_cap, Swe
     return cudaGetLastError();
 }
 
-// Band kernel when forced and a band fits shared memory.  `tmp` (at least 264
-// bytes of device memory the stream does not use yet) holds the locality
-// profile's counts on the first call.
+// Band kernel: when forced, wherever a band fits shared memory; in the
+// automatic choice, for rows that are not long (the streaming kernel's case)
+// on graphs whose locality profile admits a band and whose tables place at
+// least BAND_AUTO_SHARED of the neighbours in shared memory (the verdict is
+// kept in the context per plan).  `tmp` (at least 264 bytes of device memory
+// the stream does not use yet) holds the locality profile's counts on the
+// first call.  *chosen tells whether P now runs the band kernel.
+constexpr double BAND_AUTO_SHARED = 0.95;
+
 template <typename T, int K>
-static cudaError_t prepare_band(gr_ctx* c, SweepScratch& sc, void* tmp, SweepPlan* P, bool* ok) {
-    *ok = false;
+static cudaError_t choose_band(gr_ctx* c, SweepScratch& sc, void* tmp, SweepPlan* P, bool* chosen) {
+    *chosen = false;
+    const int want = c->sweep_kind;
+    constexpr bool f64 = sizeof(T) == 8;
+    if (want != GR_SWEEP_BAND && !(want == GR_SWEEP_AUTO && !stream_wide<T, K>(c))) return cudaSuccess;
     GR_CUDA(ensure_locality(c, tmp));
-    if (!band_usable(c, prec_of<T>(), K, true, &P->band)) return cudaSuccess;
+    BandPlan bp;
+    if (!band_usable(c, prec_of<T>(), K, want == GR_SWEEP_BAND, &bp)) return cudaSuccess;
+    const bool known = c->band_auto_ok >= 0 && c->band_auto_R == bp.R && c->band_auto_H == bp.H &&
+                       c->band_auto_grid == bp.grid && c->band_auto_f64 == (int)f64;
+    if (want == GR_SWEEP_AUTO && known && c->band_auto_ok == 0) return cudaSuccess;
     void* scr = nullptr;
     size_t scr_bytes = 0;
     if (sc.fixed()) {  // what the context does not hold is built in the rest of the fixed array
@@ -677,22 +690,35 @@ static cudaError_t prepare_band(gr_ctx* c, SweepScratch& sc, void* tmp, SweepPla
         scr_bytes = off < sc.bytes ? sc.bytes - off : 0;
         scr = scr_bytes ? sc.take(scr_bytes) : nullptr;
     }
-    GR_CUDA(band_prepare(c, P->band, sizeof(T) == 8, sc.fixed(), scr, scr_bytes, &P->runs, &P->bslots));
+    int64_t nglobal = -1;
+    const bool decide = want == GR_SWEEP_AUTO && !known;
+    GR_CUDA(band_prepare(c, bp, f64, sc.fixed(), scr, scr_bytes, &P->runs, &P->bslots, decide ? &nglobal : nullptr));
+    if (decide) {
+        c->band_auto_R = bp.R;
+        c->band_auto_H = bp.H;
+        c->band_auto_grid = bp.grid;
+        c->band_auto_f64 = (int)f64;
+        c->band_auto_ok = (double)nglobal <= (1.0 - BAND_AUTO_SHARED) * 2.0 * (double)c->m ? 1 : 0;
+        if (!c->band_auto_ok) {
+            if (!sc.fixed()) band_release(c);
+            return cudaSuccess;
+        }
+    }
     P->kind = GR_SWEEP_BAND;
-    *ok = true;
+    P->band = bp;
+    *chosen = true;
     return cudaSuccess;
 }
 
-// Kernel choice: forced by graph_reduce_set_sweep_kernel, or rows long enough
-// to fill a warp -> streaming kernel, otherwise the row-group kernel.
+// Kernel choice: forced by graph_reduce_set_sweep_kernel; automatically the
+// streaming kernel for long rows, the band kernel on banded graphs (above),
+// otherwise the row-group kernel.
 template <typename T, int K>
 static cudaError_t sweep_prepare(gr_ctx* c, SweepScratch& sc, int part_cap, void* tmp, SweepPlan* P) {
     const int want = c->sweep_kind;
-    if (want == GR_SWEEP_BAND) {
-        bool ok = false;
-        GR_CUDA((prepare_band<T, K>(c, sc, tmp, P, &ok)));
-        if (ok) return cudaSuccess;
-    }
+    bool band = false;
+    GR_CUDA((choose_band<T, K>(c, sc, tmp, P, &band)));
+    if (band) return cudaSuccess;
     if (want == GR_SWEEP_STREAM || (want == GR_SWEEP_AUTO && stream_wide<T, K>(c))) {
         P->kind = GR_SWEEP_STREAM;
         return prepare_stream<T, K>(c, sc, part_cap, P);
@@ -888,19 +914,20 @@ gr_status smooth_impl(gr_ctx* c, int K, int sweeps, double omega, uint64_t seed,
 }
 
 // The kernel choice of sweep_prepare, without launching a sweep (the band
-// kernel's locality profile is measured on first use).
+// kernel's tables and verdict are built on first use, as a smoothing call
+// would).
 template <typename T, int K>
 static cudaError_t sweep_plan_typed(gr_ctx* c, int32_t* kind) {
     const int want = c->sweep_kind;
-    if (want == GR_SWEEP_BAND) {
-        void* tmp = nullptr;
-        GR_CUDA(c->ws.get(WS_SMOOTH_PART, sizeof(double) * 2 * K * (size_t)part_capacity(c), &tmp));
-        GR_CUDA(ensure_locality(c, tmp));
-        BandPlan bp;
-        if (band_usable(c, prec_of<T>(), K, true, &bp)) {
-            *kind = GR_SWEEP_BAND;
-            return cudaSuccess;
-        }
+    void* tmp = nullptr;
+    GR_CUDA(c->ws.get(WS_SMOOTH_PART, sizeof(double) * 2 * K * (size_t)part_capacity(c), &tmp));
+    SweepScratch sc;
+    SweepPlan P;
+    bool band = false;
+    GR_CUDA((choose_band<T, K>(c, sc, tmp, &P, &band)));
+    if (band) {
+        *kind = GR_SWEEP_BAND;
+        return cudaSuccess;
     }
     *kind = (want == GR_SWEEP_STREAM || (want == GR_SWEEP_AUTO && stream_wide<T, K>(c))) ? GR_SWEEP_STREAM
                                                                                          : GR_SWEEP_ROW;

@@ -6,10 +6,11 @@ context's workspace it uses one fixed 32 MiB device array inside the library.
 It runs graph_reduce_smooth's own launch sequence, so the check is bitwise:
 through the C ABI, two calls in a row give exactly the vectors
 graph_reduce_smooth gives, for FP64, FP32 and BF16 storage, each sweep kernel
-and 0, 4 and 5 sweeps (an even count ends in place in X).  The first calls run
-on a fresh context, so the FP64 packed slots, the streaming kernel's row
-partition and the band kernel's far runs are built inside the fixed array; a
-block too large for the array is refused.  This file is named to be collected last.
+and the automatic choice, on a random and a banded graph, and 0, 4 and 5
+sweeps (an even count ends in place in X).  The first calls run on a fresh
+context, so the FP64 packed slots, the streaming kernel's row partition and
+the band kernel's tables are built inside the fixed array; a block too large
+for the array is refused.  This file is named to be collected last.
 """
 import numpy as np
 import pytest
@@ -30,13 +31,20 @@ def gr():
     return gr
 
 
+GRAPHS = {
+    "random": lambda: W.random_sparse(20011, 90000, seed=17),
+    "grid": lambda: W.grid2d(160, 125),  # banded: the automatic choice takes the band kernel
+}
+
+
 @pytest.mark.parametrize("sweeps", [0, 4, 5])
-@pytest.mark.parametrize("kernel", ["ROW", "STREAM", "BAND"])
+@pytest.mark.parametrize("kernel", ["ROW", "STREAM", "BAND", "AUTO"])
 @pytest.mark.parametrize("dtype,K", [(torch.float64, 8), (torch.float32, 16), (torch.float32, 24),
                                      (torch.bfloat16, 16)])
-def test_noalloc_equals_smooth_bitwise(gr, dtype, K, kernel, sweeps):
-    g = W.random_sparse(20011, 90000, seed=17)
-    G = gr.graph_reduce_create(g.n, g.u, g.v, g.w)  # fresh: holds no packed slots nor partition
+@pytest.mark.parametrize("graph", list(GRAPHS))
+def test_noalloc_equals_smooth_bitwise(gr, graph, dtype, K, kernel, sweeps):
+    g = GRAPHS[graph]()
+    G = gr.graph_reduce_create(g.n, g.u, g.v, g.w)  # fresh: holds no packed slots, partition nor band tables
     gr.graph_reduce_set_sweep_kernel(G, getattr(gr, "GR_SWEEP_" + kernel))
     outs = []
     for _ in range(2):
@@ -50,6 +58,8 @@ def test_noalloc_equals_smooth_bitwise(gr, dtype, K, kernel, sweeps):
     assert torch.isfinite(ref.float()).all()
     for X in outs:
         assert torch.equal(X, ref)
+    if graph == "grid" and kernel == "AUTO" and dtype == torch.float32 and K == 16:
+        assert gr.graph_reduce_sweep_plan(G, K, dtype) == gr.GR_SWEEP_BAND
 
 
 def test_noalloc_rejects_blocks_beyond_the_scratch(gr):
