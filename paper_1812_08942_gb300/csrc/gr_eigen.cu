@@ -2,16 +2,13 @@
 //
 // Coarsest level: the first k eigenpairs of L u = lambda B u (B = I ratio
 // cut, B = D normalised cut, each level's own; or the Galerkin-consistent
-// mass B_l = P^T B_(l-1) P carried from the finest I or D) from a dense
-// symmetric eigensolver (cuSOLVER syevdx for the k smallest; the coarsest
-// graph is small).  Then, level by level toward the
-// finest: U_fine = P U_coarse (the parent map), and `iters` weighted-Jacobi
+// mass B_l = P^T B_(l-1) P carried from the finest I or D) from a
+// Chebyshev-filtered subspace iteration on the coarsest graph
+// (gr_chfsi.cu).  Then, level by level toward the finest: U_fine = P U_coarse (the parent map), and `iters` weighted-Jacobi
 // iterations on (L - lambda_k B) y = 0 for every column k, the shift being the
 // coarsest eigenvalue.  Finally modified Gram-Schmidt over the columns.  Every
 // reduction is FP64 with a fixed summation order (per-block partials, then a
 // last-block finish), so results are reproducible.
-#include <cusolverDn.h>
-
 #include <vector>
 
 #include "gr_internal.cuh"
@@ -21,37 +18,6 @@ namespace gr {
 namespace {
 
 constexpr int ET = 256;
-
-// dense column-major L, or B^-1/2 L B^-1/2 for a diagonal mass b (b = NULL:
-// B = I; an entry that is not positive -- a degree-0 node under B = D --
-// counts as 1), of a small graph, thread per row
-__global__ void k_dense_laplacian(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                                  const int32_t* __restrict__ eid, const double* __restrict__ ew,
-                                  const double* __restrict__ deg, const double* __restrict__ b,
-                                  double* __restrict__ A) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    auto inv_sqrt = [&](int64_t r) { return b ? 1.0 / sqrt(b[r] > 0.0 ? b[r] : 1.0) : 1.0; };
-    const double si = inv_sqrt(i);
-    A[i + i * n] = si * deg[i] * si;
-    for (int64_t j = rowptr[i]; j < rowptr[i + 1]; ++j) {
-        const int64_t q = col[j];
-        A[i + q * n] = si * (-ew[eid[j]]) * inv_sqrt(q);
-    }
-}
-
-// first k eigenvectors (columns of the column-major A) into a row-major n x k
-// block, mapped back by B^-1/2 for a diagonal mass b (NULL: B = I)
-__global__ void k_take_eigvecs(int64_t n, int k, const double* __restrict__ A, const double* __restrict__ b,
-                               double* __restrict__ U) {
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= n * k) return;
-    const int64_t i = idx / k;
-    const int c = (int)(idx % k);
-    double x = A[i + (int64_t)c * n];
-    if (b) x = x / sqrt(b[i] > 0.0 ? b[i] : 1.0);
-    U[idx] = x;
-}
 
 // U_fine[i, :] = U_coarse[map[i], :]  (H = P, Alg. 5 step 5)
 __global__ void k_prolong(int64_t n, int k, const int32_t* __restrict__ map, const double* __restrict__ Uc,
@@ -255,11 +221,11 @@ gr_status eigensolve_impl(gr_ctx* const* levels, int nlevels, int k, int normali
     gr_ctx* f = levels[0];
     gr_ctx* c = levels[nlevels - 1];
     cudaStream_t s = f->stream;
-    const int64_t nc = c->n, n0 = f->n;
+    const int64_t n0 = f->n;
     auto blocks = [](int64_t work) { return (unsigned)ceil_div(work > 0 ? work : 1, ET); };
 
-    // scratch: dense matrix, eigenvalues, two n x k blocks at the finest size,
-    // column-major copy, reduction partials, scalars
+    // scratch: two n x k blocks at the finest size, column-major copy,
+    // reduction partials, scalars
     int64_t nmax = 0;
     for (int l = 0; l < nlevels; ++l) nmax = levels[l]->n > nmax ? levels[l]->n : nmax;
     const int RB = f->num_sms * 4;  // reduction blocks
@@ -269,11 +235,10 @@ gr_status eigensolve_impl(gr_ctx* const* levels, int nlevels, int k, int normali
         need += (bytes + 255) & ~size_t(255);
         return off;
     };
-    const size_t o_A = add(sizeof(double) * (size_t)nc * (size_t)nc), o_W = add(sizeof(double) * (size_t)nc),
-                 o_Y0 = add(sizeof(double) * (size_t)nmax * k), o_Y1 = add(sizeof(double) * (size_t)nmax * k),
+    const size_t o_Y0 = add(sizeof(double) * (size_t)nmax * k), o_Y1 = add(sizeof(double) * (size_t)nmax * k),
                  o_V = add(sizeof(double) * (size_t)n0 * k), o_T = add(sizeof(double) * (size_t)n0),
                  o_part = add(sizeof(double) * (size_t)RB), o_sc = add(sizeof(double) * 64),
-                 o_lam = add(sizeof(double) * 32), o_ctr = add(64), o_info = add(64);
+                 o_lam = add(sizeof(double) * 32), o_ctr = add(64);
     // Galerkin masses of every level: b_0 = 1 or D (degree 0 -> 1), then the
     // member sums level by level
     std::vector<size_t> o_mass;
@@ -282,8 +247,6 @@ gr_status eigensolve_impl(gr_ctx* const* levels, int nlevels, int k, int normali
     void* base;
     GR_TRY_CUDA(f, f->ws.get(WS_EIG, need, &base), "eigensolver scratch");
     char* Bp = (char*)base;
-    double* A = (double*)(Bp + o_A);
-    double* W = (double*)(Bp + o_W);
     double* Y[2] = {(double*)(Bp + o_Y0), (double*)(Bp + o_Y1)};
     double* V = (double*)(Bp + o_V);
     double* T = (double*)(Bp + o_T);
@@ -291,7 +254,6 @@ gr_status eigensolve_impl(gr_ctx* const* levels, int nlevels, int k, int normali
     double* sc = (double*)(Bp + o_sc);
     double* lam = (double*)(Bp + o_lam);
     unsigned* ctr = (unsigned*)(Bp + o_ctr);
-    int* info = (int*)(Bp + o_info);
     GR_TRY_CUDA(f, cudaMemsetAsync(ctr, 0, 64, s), "memset");
     // the diagonal mass of each level (NULL: B = I)
     std::vector<const double*> mass(nlevels, nullptr);
@@ -312,45 +274,11 @@ gr_status eigensolve_impl(gr_ctx* const* levels, int nlevels, int k, int normali
     }
 
     // 1) coarsest eigenpairs (Alg. 5 step 2, Eq. equ:lgs)
-    GR_TRY_CUDA(f, cudaMemsetAsync(A, 0, sizeof(double) * (size_t)nc * (size_t)nc, s), "memset");
-    k_dense_laplacian<<<blocks(nc), ET, 0, s>>>(nc, c->rowptr, c->col, c->eid, c->ew, c->deg, mass[nlevels - 1], A);
-    count_launch();
-    // one solver handle per host thread and device, kept for later calls
-    static thread_local cusolverDnHandle_t h = nullptr;
-    static thread_local int h_dev = -1;
-    if (h && h_dev != f->device) {
-        cusolverDnDestroy(h);
-        h = nullptr;
-    }
-    if (!h) {
-        if (cusolverDnCreate(&h) != CUSOLVER_STATUS_SUCCESS) {
-            h = nullptr;
-            return set_error(f, GR_ECUDA, "eigensolve: cusolver init");
-        }
-        h_dev = f->device;
-    }
-    if (cusolverDnSetStream(h, s) != CUSOLVER_STATUS_SUCCESS) return set_error(f, GR_ECUDA, "eigensolve: stream");
-    // only the k smallest eigenpairs (index range 1..k)
-    int lwork = 0, meig = 0;
-    if (cusolverDnDsyevdx_bufferSize(h, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_I, CUBLAS_FILL_MODE_LOWER,
-                                     (int)nc, A, (int)nc, 0.0, 0.0, 1, k, &meig, W, &lwork) != CUSOLVER_STATUS_SUCCESS)
-        return set_error(f, GR_ECUDA, "eigensolve: workspace query");
-    void* pw;
-    GR_TRY_CUDA(f, f->ws.get(WS_EIG_WORK, sizeof(double) * (size_t)(lwork > 0 ? lwork : 1), &pw), "scratch");
-    if (cusolverDnDsyevdx(h, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_I, CUBLAS_FILL_MODE_LOWER, (int)nc, A,
-                          (int)nc, 0.0, 0.0, 1, k, &meig, W, (double*)pw, lwork, info) != CUSOLVER_STATUS_SUCCESS)
-        return set_error(f, GR_ECUDA, "eigensolve: syevdx");
-    int64_t* hs = host_scratch();
-    if (!hs) return set_error(f, GR_ENOMEM, "eigensolve: pinned scratch unavailable");
-    GR_TRY_CUDA(f, cudaMemcpyAsync(hs, info, sizeof(int), cudaMemcpyDeviceToHost, s), "readback");
-    GR_TRY_CUDA(f, cudaMemcpyAsync(lam, W, sizeof(double) * (size_t)k, cudaMemcpyDeviceToDevice, s), "copy");
-    GR_TRY_CUDA(f, cudaMemcpyAsync(lambda_out, W, sizeof(double) * (size_t)k, cudaMemcpyDeviceToHost, s), "copy");
-    GR_TRY_CUDA(f, cudaStreamSynchronize(s), "sync");
-    if (((int*)hs)[0] != 0 || meig < k)
-        return set_error(f, GR_ECUDA, "eigensolve: the dense eigensolver did not converge");
     int cur = 0;
-    k_take_eigvecs<<<blocks(nc * k), ET, 0, s>>>(nc, k, A, mass[nlevels - 1], Y[cur]);
-    count_launch();
+    {
+        const gr_status st = coarsest_eigenpairs(c, mass[nlevels - 1], k, f->ws, s, lam, lambda_out, Y[cur], nullptr);
+        if (st != GR_OK) return set_error(f, st, c->last_error);
+    }
 
     // 2) map and smooth, level by level (Alg. 5 steps 4-10)
     for (int l = nlevels - 2; l >= 0; --l) {
@@ -421,6 +349,8 @@ gr_status eigensolve_impl(gr_ctx* const* levels, int nlevels, int k, int normali
             k_dot<<<rb, ET, 0, s>>>(n0, ui, bu, part, ctr, sc + 2 * i + 1);
             count_launch();
         }
+        int64_t* hs = host_scratch();
+        if (!hs) return set_error(f, GR_ENOMEM, "eigensolve: pinned scratch unavailable");
         double* hq = (double*)hs;  // 64 B: up to 4 pairs at a time
         for (int i0 = 0; i0 < k; i0 += 4) {
             const int cnt = k - i0 < 4 ? k - i0 : 4;

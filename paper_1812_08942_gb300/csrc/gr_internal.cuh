@@ -139,6 +139,15 @@ cudaError_t sweep_band(gr_ctx* c, int prec, int K, const BandPlan& bp, const int
                        const void* Ain, void* Aout, double omega, const double* st_in, double* part, int part_cap,
                        unsigned* counter, double* st_out, int* err);
 
+// The k smallest eigenpairs of L u = lambda B u on graph c (b: the diagonal
+// of B, NULL for B = I; entries that are not positive count as 1), by a
+// Chebyshev-filtered subspace iteration (gr_chfsi.cu): lam_dev (device) and
+// lam_host (host), k eigenvalues ascending; U (device, n x k row-major) the
+// eigenvectors; scratch from ws slot WS_EIG_WORK; *iters (may be NULL) the
+// filter iterations run.  GR_ECUDA if it does not converge.
+gr_status coarsest_eigenpairs(gr_ctx* c, const double* b, int k, Workspace& ws, cudaStream_t s, double* lam_dev,
+                              double* lam_host, double* U, int* iters);
+
 // primitives (gr_prims.cu)
 cudaError_t scan_exclusive_i64(const int64_t* in, int64_t* out, int64_t count, Workspace& ws,
                                cudaStream_t s);

@@ -3,8 +3,8 @@
 The hierarchy comes from the oracle's own reduction; the GPU contexts are
 rebuilt from the oracle's aggregate maps with graph_reduce_coarsen, so both
 sides solve the same problem and no oracle input comes from the CUDA path.
-Eigenvectors are compared up to the sign of each column (a dense eigensolver
-fixes none); the graphs are connected and have random weights, so the
+Eigenvectors are compared up to the sign of each column (the coarsest
+solver, a Chebyshev-filtered subspace iteration, fixes none); the graphs are connected and have random weights, so the
 eigenvalues are simple.  k = 2, 4, 8, 16, 32 take the row-chunk smoothing
 kernel, other k the thread-per-entry one.  Every case runs with each level's
 own mass B (Alg. 5 as written) and with the Galerkin-consistent mass
@@ -85,6 +85,22 @@ def test_eigensolve_single_level_and_no_smoothing(gr, oracle_mod):
     assert np.allclose(lam, ref, atol=1e-10) and np.allclose(rq, ref, atol=1e-10)
     Uh = U.cpu().numpy()
     assert np.allclose(Uh.T @ Uh, np.eye(5), atol=1e-12)
+    # a graph no larger than the iteration's block (k + 8 columns): one
+    # Rayleigh-Ritz step over the whole space, ratio and normalised cut
+    t = W.random_sparse(12, 30, seed=31)
+    assert oracle_mod.n_components(t.n, t.u, t.v) == 1
+    T = gr.graph_reduce_create(t.n, t.u, t.v, t.w)
+    Lt = oracle_mod.dense_laplacian(t.n, t.u, t.v, t.w)
+    for normalized in (False, True):
+        Ut, lt, _ = gr.graph_reduce_eigensolve([T], 8, normalized, 0.7, 0)
+        dt = np.diag(Lt) if normalized else np.ones(t.n)
+        ref_t = np.sort(np.linalg.eigvalsh(Lt / np.sqrt(np.outer(dt, dt))))[:8]
+        assert np.allclose(lt, ref_t, atol=1e-12)
+        Uh = Ut.cpu().numpy()
+        assert np.allclose(Uh.T @ Uh, np.eye(8), atol=1e-12)
+        if not normalized:  # B = I: the orthonormalised columns stay eigenvectors
+            res = Lt @ Uh - Uh * np.asarray(lt)[None, :]
+            assert np.max(np.abs(res)) <= 1e-10
     # iters = 0: the finest block is the mapped coarse block, orthonormalised
     graphs, maps, ctxs = _hierarchy(gr, oracle_mod, g, 100)
     Ur, _ = oracle_mod.multilevel_eigensolve(graphs, maps, 4, False, 0.7, 0)
