@@ -504,16 +504,41 @@ def sparse_laplacian(n, u, v, w):
 
 def smallest_nontrivial_eigs(n, u, v, w, k=10, dense_max=8000):
     """The k smallest eigenvalues after skipping one zero per connected
-    component.  Dense eigh when n <= dense_max, else shift-invert eigsh."""
-    c = n_components(n, u, v)
-    if n <= dense_max:
-        L = sparse_laplacian(n, u, v, w).toarray()
-        ev = np.linalg.eigvalsh(L)
-        return ev[c:c + k]
-    from scipy.sparse.linalg import eigsh
-    L = sparse_laplacian(n, u, v, w)
-    deg = np.asarray(L.diagonal())
-    sigma = -1e-3 * float(deg.mean())
-    ev = eigsh(L, k=k + c, sigma=sigma, which="LM", return_eigenvectors=False, tol=1e-12)
-    ev = np.sort(ev)
-    return ev[c:c + k]
+    component.  The spectrum of L is the union of its components' spectra,
+    each holding one zero, so each component is solved on its own: dense eigh
+    when it has at most dense_max nodes, else shift-invert eigsh from a fixed
+    start vector (one zero, so no repeated eigenvalue at the bottom); the
+    components' nontrivial eigenvalues are merged and the k smallest returned."""
+    from scipy.sparse import coo_matrix
+    from scipy.sparse.csgraph import connected_components
+    u = np.asarray(u, np.int64)
+    v = np.asarray(v, np.int64)
+    A = coo_matrix((np.ones(len(u)), (u, v)), shape=(n, n))
+    c, lab = connected_components(A, directed=False)
+    order = np.argsort(lab, kind="stable")
+    starts = np.searchsorted(lab[order], np.arange(c + 1))
+    local = np.empty(n, np.int64)
+    local[order] = np.arange(n) - starts[lab[order]]
+    elab = lab[u]
+    eorder = np.argsort(elab, kind="stable")
+    estarts = np.searchsorted(elab[eorder], np.arange(c + 1))
+    found = []
+    for comp in range(c):
+        nc = int(starts[comp + 1] - starts[comp])
+        if nc < 2:
+            continue
+        e = eorder[estarts[comp]:estarts[comp + 1]]
+        cu, cv, cw = local[u[e]], local[v[e]], np.asarray(w)[e]
+        if nc <= dense_max:
+            ev = np.linalg.eigvalsh(sparse_laplacian(nc, cu, cv, cw).toarray())
+            found.append(ev[1:1 + k])
+        else:
+            from scipy.sparse.linalg import eigsh
+            L = sparse_laplacian(nc, cu, cv, cw)
+            sigma = -1e-3 * float(np.asarray(L.diagonal()).mean())
+            v0 = np.cos(np.arange(nc) * 0.7) + 0.5
+            kk = min(k + 1, nc - 2)
+            ev = np.sort(eigsh(L, k=kk, sigma=sigma, which="LM", v0=v0, tol=1e-12, return_eigenvectors=False))
+            found.append(ev[1:1 + k])
+    allev = np.sort(np.concatenate(found)) if found else np.zeros(0)
+    return allev[:k]

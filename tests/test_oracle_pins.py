@@ -923,3 +923,20 @@ def test_scale_edges_cap_binds_on_a_matching(oracle_mod):
                                      kmax=kmax, eps=0.0)
     step = delta_bar ** (1.0 / kmax)
     assert np.allclose([x[1] for x in h4], [step ** (k + 1) for k in range(kmax)], rtol=0, atol=1e-13)
+
+
+def test_smallest_nontrivial_eigs_per_component(oracle_mod):
+    # the per-component solve against one dense eigh of the whole Laplacian
+    # with its c zeros skipped, through both the dense and the sparse branch
+    parts = [W.random_sparse(60, 200, seed=s) for s in range(5)] + [W.grid2d(7, 9)]
+    u = np.concatenate([q.u.astype(np.int64) + 60 * i for i, q in enumerate(parts)])
+    v = np.concatenate([q.v.astype(np.int64) + 60 * i for i, q in enumerate(parts)])
+    w = np.concatenate([q.w for q in parts])
+    n = 60 * 5 + 63 + 4  # four isolated nodes at the end
+    L = oracle_mod.sparse_laplacian(n, u, v, w).toarray()
+    c = oracle_mod.n_components(n, u, v)
+    assert c == 10
+    ref = np.linalg.eigvalsh(L)[c:c + 12]
+    for dmax in (8000, 40):
+        got = oracle_mod.smallest_nontrivial_eigs(n, u, v, w, 12, dense_max=dmax)
+        assert np.allclose(got, ref, rtol=1e-10, atol=1e-11), (dmax, got, ref)
