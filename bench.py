@@ -576,7 +576,7 @@ def main():
         del G32, lv32, G64, lv64
 
     # Multilevel Laplacian eigensolver (Alg. 5) on a deeper reduction of the
-    # same graph (down to 1,024 nodes, where the dense FP64 eigensolve runs):
+    # same graph (down to 1,024 nodes, where the coarsest eigenpairs are found):
     # k = 8 ratio-cut eigenvectors, 10 shifted Jacobi iterations
     # per level.  The smoothing time is the difference against 0 iterations;
     # its roofline counts, per iteration on each level, the CSR slots

@@ -8,7 +8,9 @@
 // Method: Chebyshev-filtered subspace iteration (Zhou and Saad, "A Chebyshev-
 // Davidson algorithm for large symmetric eigenproblems", SIAM J. Matrix Anal.
 // Appl. 29 (2007); Zhou, Saad, Tiago and Chelikowsky, J. Comput. Phys. 219
-// (2006)) on a block of p = k + max(8, k/2) columns (at most n):
+// (2006)) on a block of p = k + max(8, k/2) columns (at most n; doubled, up
+// to 64, while the block's largest Ritz value is 0 to within 1e-10 beta --
+// a null space wider than the block, as on graphs of many components):
 //   1. X: a seeded random block, orthonormalised, Rayleigh-Ritz'd.
 //   2. Repeat: Y = T_d((A - c I) / e) X / T_d((0 - c) / e), the Chebyshev
 //      polynomial of degree d that is bounded by 1 on [alpha, beta] (alpha =
@@ -19,9 +21,11 @@
 //      by its eigenvalues^-1/2, after unit column scaling); Rayleigh-Ritz
 //      (eigenpairs of Y^T A Y rotate Y); until the k first Ritz pairs have
 //      residuals ||A x - theta x|| <= 1e-13 beta.
-//   The degree is capped so that the filter grows by at most 1e6 between 0
-//   and alpha, which bounds the filtered block's condition number and keeps
-//   the SVQB steps accurate in FP64.
+//   The degree is the largest (up to 4,000) for which the filter grows by at
+//   most 1e6 between 0 and alpha, which bounds the filtered block's condition
+//   number and keeps the SVQB steps accurate in FP64; a small alpha / beta
+//   (eigenvalues clustered near 0 against a wide spectrum) thus gets a high
+//   degree rather than many iterations.
 // The small p x p symmetric eigenproblems (Gram and Rayleigh-Ritz matrices,
 // p <= 64) run in one thread block by the cyclic Jacobi method with the
 // round-robin parallel ordering (Golub and Van Loan, Matrix Computations,
@@ -42,9 +46,10 @@ constexpr int CF_PMAX = 64;       // block columns at most (k <= 32)
 constexpr int CF_ROWS = 16;       // rows staged per step of a Gram partial
 constexpr int CF_SWEEPS = 60;     // Jacobi sweeps at most
 constexpr int CF_MAX_ITERS = 400; // filter iterations at most
-constexpr int CF_DEG_MAX = 40;
+constexpr int CF_DEG_MAX = 4000; // filter degree at most
 constexpr double CF_GROWTH = 1e6; // filter growth between 0 and alpha at most
 constexpr double CF_TOL = 1e-13;  // residual bar, relative to beta
+constexpr double CF_DENSE_RATE = 0.05;  // per-degree rate below which small graphs go dense
 
 // S = B^-1/2 as a vector (b = NULL: B = I)
 __global__ void k_cf_scale(int64_t n, const double* __restrict__ b, double* __restrict__ sc) {
@@ -70,6 +75,17 @@ __global__ void k_cf_init(int64_t n, int p, uint64_t seed, double* __restrict__ 
         X[idx] = cf_uniform(seed, (uint64_t)idx);
 }
 
+// Y (n x pn) = [X (n x p) | seeded columns]
+__global__ void k_cf_widen(int64_t n, int p, int pn, uint64_t seed, const double* __restrict__ X,
+                           double* __restrict__ Y) {
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n * pn;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = idx / pn;
+        const int c = (int)(idx % pn);
+        Y[idx] = c < p ? X[i * p + c] : cf_uniform(seed, (uint64_t)idx);
+    }
+}
+
 // Gershgorin bound of A = S L S: max_i s_i (s_i deg_i + sum_j w_ij s_j), as
 // the bit pattern of a non-negative double (an integer max is exact and
 // order-free).  Warp per row.
@@ -92,28 +108,80 @@ __global__ void k_cf_bound(int64_t n, const int64_t* __restrict__ rowptr, const 
     }
 }
 
-// Out = c1 (A Y) + c2 Y + c3 Yp (Yp may be NULL), n x p row-major; warp per
-// row, lanes over columns; the row's products in slot order.
+// Entries of A = S L S in the CSR's slots: off-diagonal -s_i w_ij s_j, and
+// the diagonal s_i^2 deg_i per row
+__global__ void k_cf_values(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                            const int32_t* __restrict__ eid, const double* __restrict__ ew,
+                            const double* __restrict__ deg, const double* __restrict__ sc, double* __restrict__ av,
+                            double* __restrict__ ad) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double si = sc[i];
+        ad[i] = si * si * deg[i];
+        for (int64_t j = rowptr[i]; j < rowptr[i + 1]; ++j) av[j] = -si * ew[eid[j]] * sc[col[j]];
+    }
+}
+
+// Out = c1 (A Y) + c2 Y + c3 Yp (Yp may be NULL), n x p row-major, A from
+// its slot values av and diagonal ad.  Short rows: warp per row, lanes over
+// columns, the row's products in slot order.
 __global__ void k_cf_apply(int64_t n, int p, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                           const int32_t* __restrict__ eid, const double* __restrict__ ew,
-                           const double* __restrict__ deg, const double* __restrict__ sc, double c1, double c2,
+                           const double* __restrict__ av, const double* __restrict__ ad, double c1, double c2,
                            double c3, const double* __restrict__ Y, const double* __restrict__ Yp,
                            double* __restrict__ Out) {
     const int lane = threadIdx.x & 31;
     for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n;
          i += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-        const double si = sc[i];
         const int64_t j0 = rowptr[i], j1 = rowptr[i + 1];
         for (int q = lane; q < p; q += 32) {
             const double yi = Y[i * p + q];
-            double acc = deg[i] * si * yi;
-            for (int64_t j = j0; j < j1; ++j) {
-                const int32_t c = col[j];
-                acc -= ew[eid[j]] * sc[c] * Y[(int64_t)c * p + q];
-            }
-            double o = c1 * (si * acc) + c2 * yi;
+            double acc = ad[i] * yi;
+            for (int64_t j = j0; j < j1; ++j) acc += av[j] * Y[(int64_t)col[j] * p + q];
+            double o = c1 * acc + c2 * yi;
             if (Yp) o += c3 * Yp[i * p + q];
             Out[i * p + q] = o;
+        }
+    }
+}
+
+// The same for long rows (dense coarse graphs): warp per row, lanes over the
+// row's slots, 16 columns at a time in registers; each lane's partial sums in
+// slot order, then a fixed butterfly over the lanes.
+constexpr int CF_QC = 16;
+__global__ void k_cf_apply_long(int64_t n, int p, const int64_t* __restrict__ rowptr,
+                                const int32_t* __restrict__ col, const double* __restrict__ av,
+                                const double* __restrict__ ad, double c1, double c2, double c3,
+                                const double* __restrict__ Y, const double* __restrict__ Yp,
+                                double* __restrict__ Out) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n;
+         i += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int64_t j0 = rowptr[i], j1 = rowptr[i + 1];
+        for (int q0 = 0; q0 < p; q0 += CF_QC) {
+            double acc[CF_QC];
+#pragma unroll
+            for (int u = 0; u < CF_QC; ++u) acc[u] = 0.0;
+            for (int64_t j = j0 + lane; j < j1; j += 32) {
+                const double a = av[j];
+                const double* yr = Y + (int64_t)col[j] * p + q0;
+#pragma unroll
+                for (int u = 0; u < CF_QC; ++u)
+                    if (q0 + u < p) acc[u] += a * yr[u];
+            }
+#pragma unroll
+            for (int u = 0; u < CF_QC; ++u)
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) acc[u] += __shfl_xor_sync(0xffffffffu, acc[u], o);
+            if (lane < CF_QC && q0 + lane < p) {
+                double a = 0.0;
+#pragma unroll
+                for (int u = 0; u < CF_QC; ++u)
+                    if (u == lane) a = acc[u];
+                const int q = q0 + lane;
+                const double yi = Y[i * p + q];
+                double o = c1 * (ad[i] * yi + a) + c2 * yi;
+                if (Yp) o += c3 * Yp[i * p + q];
+                Out[i * p + q] = o;
+            }
         }
     }
 }
@@ -365,11 +433,19 @@ __global__ void __launch_bounds__(CT) k_cf_small(int p, int mode, const double* 
 // The k smallest eigenpairs of L u = lambda B u on graph c (b: the diagonal
 // of B, NULL for B = I): lam_dev / lam_host (k ascending eigenvalues),
 // U (n x k row-major, column j an eigenvector for lam[j]); scratch from the
-// workspace slot WS_EIG_WORK of ws.  *iters: the filter iterations run.
+// workspace slot WS_EIG_WORK of ws.  *iters: the filter iterations run (-1:
+// handed to the dense route).
 gr_status coarsest_eigenpairs(gr_ctx* c, const double* b, int k, Workspace& ws, cudaStream_t s, double* lam_dev,
                               double* lam_host, double* U, int* iters) {
     const int64_t n = c->n;
-    const int p = (int)(n < (int64_t)(k + (k / 2 > 8 ? k / 2 : 8)) ? n : (int64_t)(k + (k / 2 > 8 ? k / 2 : 8)));
+    // graphs up to DENSE_EIG_MAX nodes switch to the dense route as soon as
+    // the filter would need thousands of degrees (below)
+    auto go_dense = [&]() -> gr_status {
+        if (iters) *iters = -1;
+        return dense_eigenpairs(c, b, k, ws, s, lam_dev, lam_host, U);
+    };
+    int p = (int)(n < (int64_t)(k + (k / 2 > 8 ? k / 2 : 8)) ? n : (int64_t)(k + (k / 2 > 8 ? k / 2 : 8)));
+    const int pcap = (int)(n < (int64_t)CF_PMAX ? n : (int64_t)CF_PMAX);
     if (k < 1 || k > 32 || p > CF_PMAX || n < k) return set_error(c, GR_EINVAL, "eigensolve: k out of range");
     const int nbg = (int)(ceil_div(n, 64) < (int64_t)c->num_sms ? ceil_div(n, 64) : (int64_t)c->num_sms);
     const int nb = nbg > 0 ? nbg : 1;
@@ -379,11 +455,13 @@ gr_status coarsest_eigenpairs(gr_ctx* c, const double* b, int k, Workspace& ws, 
         need += (bytes + 255) & ~size_t(255);
         return off;
     };
-    const size_t blk = sizeof(double) * (size_t)n * p;
+    // every block sized for the widest block the iteration may grow to
+    const size_t blk = sizeof(double) * (size_t)n * pcap;
     const size_t o_X = add(blk), o_AX = add(blk), o_Y0 = add(blk), o_Y1 = add(blk), o_Y2 = add(blk),
-                 o_part = add(sizeof(double) * (size_t)nb * p * p), o_G = add(sizeof(double) * p * p),
-                 o_T = add(sizeof(double) * p * p), o_th = add(sizeof(double) * CF_PMAX),
-                 o_rn = add(sizeof(double) * CF_PMAX), o_bd = add(64), o_sc = add(sizeof(double) * (size_t)n);
+                 o_part = add(sizeof(double) * (size_t)nb * pcap * pcap), o_G = add(sizeof(double) * pcap * pcap),
+                 o_T = add(sizeof(double) * pcap * pcap), o_th = add(sizeof(double) * CF_PMAX),
+                 o_rn = add(sizeof(double) * CF_PMAX), o_bd = add(64), o_sc = add(sizeof(double) * (size_t)n),
+                 o_ad = add(sizeof(double) * (size_t)n), o_av = add(sizeof(double) * (size_t)(2 * c->m > 0 ? 2 * c->m : 1));
     void* base;
     GR_TRY_CUDA(c, ws.get(WS_EIG_WORK, need, &base), "eigensolve: scratch");
     char* Bp = (char*)base;
@@ -397,16 +475,23 @@ gr_status coarsest_eigenpairs(gr_ctx* c, const double* b, int k, Workspace& ws, 
     double* rn = (double*)(Bp + o_rn);
     unsigned long long* bd = (unsigned long long*)(Bp + o_bd);
     double* sc = (double*)(Bp + o_sc);
+    double* ad = (double*)(Bp + o_ad);
+    double* av = (double*)(Bp + o_av);
+    const bool long_rows = n > 0 && 2.0 * (double)c->m / (double)n >= 64.0;
     const unsigned wgrid = (unsigned)(ceil_div(n * 32, CT) < (int64_t)c->num_sms * 8 ? ceil_div(n * 32, CT)
                                                                                      : (int64_t)c->num_sms * 8);
-    const unsigned egrid = (unsigned)(ceil_div(n * p, CT) < (int64_t)c->num_sms * 8 ? ceil_div(n * p, CT)
-                                                                                    : (int64_t)c->num_sms * 8);
-    const size_t small_smem = sizeof(double) * 2 * p * p;
-    GR_TRY_CUDA(c, cudaFuncSetAttribute(k_cf_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)small_smem),
+    const unsigned egrid = (unsigned)(ceil_div(n * pcap, CT) < (int64_t)c->num_sms * 8 ? ceil_div(n * pcap, CT)
+                                                                                        : (int64_t)c->num_sms * 8);
+    GR_TRY_CUDA(c, cudaFuncSetAttribute(k_cf_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)(sizeof(double) * 2 * pcap * pcap)),
                 "eigensolve: smem");
+    auto small_smem = [&]() { return sizeof(double) * 2 * p * p; };
 
     auto apply = [&](double c1, double c2, double c3, const double* Y, const double* Yp, double* Out) {
-        k_cf_apply<<<wgrid, CT, 0, s>>>(n, p, c->rowptr, c->col, c->eid, c->ew, c->deg, sc, c1, c2, c3, Y, Yp, Out);
+        if (long_rows)
+            k_cf_apply_long<<<wgrid, CT, 0, s>>>(n, p, c->rowptr, c->col, av, ad, c1, c2, c3, Y, Yp, Out);
+        else
+            k_cf_apply<<<wgrid, CT, 0, s>>>(n, p, c->rowptr, c->col, av, ad, c1, c2, c3, Y, Yp, Out);
         count_launch();
     };
     auto gram = [&](const double* Y1, const double* Y2) {
@@ -423,7 +508,7 @@ gr_status coarsest_eigenpairs(gr_ctx* c, const double* b, int k, Workspace& ws, 
     auto svqb2 = [&](int yi) {
         for (int pass = 0; pass < 2; ++pass) {
             gram(Yb[yi], Yb[yi]);
-            k_cf_small<<<1, CT, small_smem, s>>>(p, 0, G, T, nullptr);
+            k_cf_small<<<1, CT, small_smem(), s>>>(p, 0, G, T, nullptr);
             count_launch();
             const int zi = (yi + 1) % 3;
             mul(Yb[yi], T, Yb[zi]);
@@ -438,7 +523,7 @@ gr_status coarsest_eigenpairs(gr_ctx* c, const double* b, int k, Workspace& ws, 
         double* AY = Yb[(yi + 1) % 3];
         apply(1.0, 0.0, 0.0, Yb[yi], nullptr, AY);
         gram(Yb[yi], AY);
-        k_cf_small<<<1, CT, small_smem, s>>>(p, 1, G, T, th);
+        k_cf_small<<<1, CT, small_smem(), s>>>(p, 1, G, T, th);
         count_launch();
         mul(Yb[yi], T, X);
         mul(AY, T, AX);
@@ -457,6 +542,8 @@ gr_status coarsest_eigenpairs(gr_ctx* c, const double* b, int k, Workspace& ws, 
     count_launch();
     GR_TRY_CUDA(c, cudaMemsetAsync(bd, 0, sizeof(unsigned long long), s), "memset");
     k_cf_bound<<<wgrid, CT, 0, s>>>(n, c->rowptr, c->col, c->eid, c->ew, c->deg, sc, bd);
+    count_launch();
+    k_cf_values<<<(unsigned)ceil_div(n, CT), CT, 0, s>>>(n, c->rowptr, c->col, c->eid, c->ew, c->deg, sc, av, ad);
     count_launch();
     unsigned long long hb = 0;
     GR_TRY_CUDA(c, cudaMemcpyAsync(&hb, bd, sizeof(hb), cudaMemcpyDeviceToHost, s), "readback");
@@ -479,7 +566,19 @@ gr_status coarsest_eigenpairs(gr_ctx* c, const double* b, int k, Workspace& ws, 
     // a block of all n columns spans the space: its Rayleigh-Ritz pairs are exact
     while (p < n && !converged()) {
         if (++it > CF_MAX_ITERS) return set_error(c, GR_ECUDA, "eigensolve: the coarsest eigenpairs did not converge");
-        const double alpha = hv[p - 1];
+        if (hv[p - 1] <= 1e-10 * beta && p < pcap && n <= DENSE_EIG_MAX) return go_dense();
+        if (hv[p - 1] <= 1e-10 * beta && p < pcap) {
+            // the block lies in a cluster at 0 at least p wide (a graph of many
+            // components): widen it with fresh seeded columns and start over
+            const int pn = 2 * p < pcap ? 2 * p : pcap;
+            k_cf_widen<<<egrid, CT, 0, s>>>(n, p, pn, 0x5EEDC0A25E5Eull + (uint64_t)it, X, Yb[0]);
+            count_launch();
+            p = pn;
+            yi = svqb2(0);
+            GR_TRY_CUDA(c, rayleigh_ritz(yi), "eigensolve: Rayleigh-Ritz");
+            continue;
+        }
+        const double alpha = hv[p - 1] > 1e-10 * beta ? hv[p - 1] : 1e-10 * beta;
         // beta bounds the spectrum from above; should the block's top Ritz value
         // reach it, damp just above that value
         const double top = beta > alpha * (1.0 + 1e-9) ? beta : alpha * (1.0 + 1e-6) + 1e-300;
@@ -489,6 +588,14 @@ gr_status coarsest_eigenpairs(gr_ctx* c, const double* b, int k, Workspace& ws, 
         const double g = acosh(-x0);
         const double dmax = g > 0.0 ? acosh(CF_GROWTH) / g : (double)CF_DEG_MAX;
         const int d = dmax < 2.0 ? 2 : (dmax > (double)CF_DEG_MAX ? CF_DEG_MAX : (int)dmax);
+        // after two filtered passes the Ritz values predict the rate: the
+        // slowest wanted pair gains acosh(t) per degree against [alpha, top];
+        // below CF_DENSE_RATE (some 600 degrees for 1e-13) the dense route is
+        // cheaper, where the graph is small enough for it
+        if (it > 2 && n <= DENSE_EIG_MAX) {
+            const double tw = (alpha + top - 2.0 * hv[k - 1]) / (top - alpha);
+            if (!(tw > 1.0) || acosh(tw) < CF_DENSE_RATE) return go_dense();
+        }
         // rho_j = T_j(x0); Y_{j+1} = (2 rho_j / rho_{j+1}) x(A) Y_j - (rho_{j-1} / rho_{j+1}) Y_{j-1}
         double rm1 = 1.0, r0 = x0;
         int cur = (yi + 1) % 3, prv = yi;  // X is the current Ritz block

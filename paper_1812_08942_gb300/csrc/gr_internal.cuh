@@ -147,6 +147,13 @@ cudaError_t sweep_band(gr_ctx* c, int prec, int K, const BandPlan& bp, const int
 // filter iterations run.  GR_ECUDA if it does not converge.
 gr_status coarsest_eigenpairs(gr_ctx* c, const double* b, int k, Workspace& ws, cudaStream_t s, double* lam_dev,
                               double* lam_host, double* U, int* iters);
+// The same for graphs of at most DENSE_EIG_MAX nodes by the dense route
+// (gr_dense_eig.cu: Householder tridiagonalisation, bisection, inverse
+// iteration); coarsest_eigenpairs hands such graphs to it when the filtered
+// iteration would converge slowly.
+constexpr int DENSE_EIG_MAX = 4096;
+gr_status dense_eigenpairs(gr_ctx* c, const double* b, int k, Workspace& ws, cudaStream_t s, double* lam_dev,
+                           double* lam_host, double* U);
 
 // primitives (gr_prims.cu)
 cudaError_t scan_exclusive_i64(const int64_t* in, int64_t* out, int64_t count, Workspace& ws,

@@ -4,7 +4,8 @@ The hierarchy comes from the oracle's own reduction; the GPU contexts are
 rebuilt from the oracle's aggregate maps with graph_reduce_coarsen, so both
 sides solve the same problem and no oracle input comes from the CUDA path.
 Eigenvectors are compared up to the sign of each column (the coarsest
-solver, a Chebyshev-filtered subspace iteration, fixes none); the graphs are connected and have random weights, so the
+solver -- Householder tridiagonalisation, bisection and inverse iteration up
+to 4,096 nodes, a Chebyshev-filtered subspace iteration beyond -- fixes none); the graphs are connected and have random weights, so the
 eigenvalues are simple.  k = 2, 4, 8, 16, 32 take the row-chunk smoothing
 kernel, other k the thread-per-entry one.  Every case runs with each level's
 own mass B (Alg. 5 as written) and with the Galerkin-consistent mass
@@ -106,6 +107,48 @@ def test_eigensolve_single_level_and_no_smoothing(gr, oracle_mod):
     Ur, _ = oracle_mod.multilevel_eigensolve(graphs, maps, 4, False, 0.7, 0)
     U0, _, _ = gr.graph_reduce_eigensolve(ctxs, 4, False, 0.7, 0)
     assert _compare(U0, Ur, 1e-9)
+
+
+def test_eigensolve_many_components(gr, oracle_mod):
+    # 24 components of 40 nodes with weights up to ~250: the null space is
+    # wider than the iteration's block for k = 8 (the block grows) and the
+    # nonzero eigenvalues sit far below the spectral bound
+    parts = [W.random_sparse(40, 120, seed=100 + i) for i in range(24)]
+    u = np.concatenate([q.u + 40 * i for i, q in enumerate(parts)]).astype(np.int32)
+    v = np.concatenate([q.v + 40 * i for i, q in enumerate(parts)]).astype(np.int32)
+    w = np.concatenate([q.w * 50.0 for q in parts])
+    n = 40 * len(parts)
+    assert oracle_mod.n_components(n, u, v) == 24
+    G = gr.graph_reduce_create(n, u, v, w)
+    L = oracle_mod.dense_laplacian(n, u, v, w)
+    ev = np.sort(np.linalg.eigvalsh(L))
+    beta = np.max(np.sum(np.abs(L), 1))
+    for k in (8, 32):
+        U, lam, rq = gr.graph_reduce_eigensolve([G], k, False, 0.7, 0)
+        assert np.allclose(lam, ev[:k], rtol=1e-10, atol=1e-11 * beta), (k, lam, ev[:k])
+        Uh = U.cpu().numpy()
+        assert np.allclose(Uh.T @ Uh, np.eye(k), atol=1e-12)
+        # columns of a repeated eigenvalue are any basis of its eigenspace:
+        # check the residuals, not the vectors
+        res = L @ Uh - Uh * np.asarray(lam)[None, :]
+        assert np.max(np.abs(res)) <= 1e-10 * beta, (k, np.max(np.abs(res)))
+
+
+def test_eigensolve_large_coarsest_level(gr, oracle_mod):
+    # a coarsest level above the dense route's 4,096 nodes takes the
+    # Chebyshev-filtered subspace iteration: eigenvalues against shift-invert
+    # Lanczos, eigenpairs by their residuals, ratio cut
+    g = W.mesh3d(20, 16, 17, seed=41)
+    assert g.n > 4096 and oracle_mod.n_components(g.n, g.u, g.v) == 1
+    G = gr.graph_reduce_create(g.n, g.u, g.v, g.w)
+    U, lam, rq = gr.graph_reduce_eigensolve([G], 8, False, 0.7, 0)
+    ref = oracle_mod.smallest_nontrivial_eigs(g.n, g.u, g.v, g.w, 7)
+    assert abs(lam[0]) <= 1e-11
+    assert np.allclose(lam[1:], ref, rtol=1e-9, atol=1e-11), (lam, ref)
+    L = oracle_mod.sparse_laplacian(g.n, g.u, g.v, g.w)
+    Uh = U.cpu().numpy()
+    res = L @ Uh - Uh * np.asarray(lam)[None, :]
+    assert np.max(np.abs(res)) <= 1e-9
 
 
 def test_eigensolve_rejects_bad_requests(gr, oracle_mod):
