@@ -216,6 +216,7 @@ constexpr int ST_NB = 16;              // ring batches per warp
 constexpr int ST_D = 8;                // batches kept in flight ahead of use
 constexpr int ST_RING = ST_NB * 32;    // ring slots per warp
 constexpr int ST_SPAN = ST_NB - ST_D;  // batches one window may span
+static_assert(ST_SPAN >= 1, "a window must fit the ring");
 constexpr int ST_ROW_COST = 8;         // partition weight of a row, in slots
 
 template <typename T>
@@ -862,7 +863,6 @@ template <typename T, int K>
 static cudaError_t run_test_vectors(gr_ctx* c, uint64_t seed, int level, T* X) {
     cudaStream_t s = c->stream;
     const int64_t n = c->n;
-    constexpr int GP = RowLayout<T, K>::GP;
     void *p_st, *p_part;
     GR_CUDA(c->ws.get(WS_SMOOTH_STATS, sizeof(double) * 4 * K + 64, &p_st));
     double* st0 = (double*)p_st;
@@ -1190,7 +1190,7 @@ static gr_status run_smooth_gs(gr_ctx* c, int sweeps, double omega, uint64_t see
     }
     cudaStream_t s = c->stream;
     const int64_t n = c->n;
-    constexpr int G = RowLayout<T, K>::G, GP = RowLayout<T, K>::GP;
+    constexpr int G = RowLayout<T, K>::G;
     void *p_st, *p_part;
     GR_TRY_CUDA(c, c->ws.get(WS_SMOOTH_STATS, sizeof(double) * 4 * K + 64, &p_st), "scratch");
     double* st = (double*)p_st;

@@ -58,25 +58,4 @@ __device__ void finish_stats(const double* __restrict__ part, int nblocks, int64
     }
 }
 
-// Compensated FP32 summation (Knuth's TwoSum; the product error of y*y by
-// one FMA): s + c carries the running sum to about twice FP32's precision,
-// whatever the number of terms, at FP32 cost.  The explicitly rounded
-// intrinsics keep the compiler from contracting or reassociating the steps.
-__device__ __forceinline__ void csum_add(float& s, float& c, float y) {
-    const float t = __fadd_rn(s, y);
-    const float bp = __fsub_rn(t, s);
-    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(y, bp));
-    c = __fadd_rn(c, err);
-    s = t;
-}
-__device__ __forceinline__ void csum_sq(float& s, float& c, float y) {
-    const float p = __fmul_rn(y, y);
-    const float e = __fmaf_rn(y, y, -p);  // y*y - p exactly
-    csum_add(s, c, p);
-    c = __fadd_rn(c, e);
-}
-// FP64 blocks accumulate in FP64 directly
-__device__ __forceinline__ void csum_add(double& s, double&, double y) { s += y; }
-__device__ __forceinline__ void csum_sq(double& s, double&, double y) { s += y * y; }
-
 }  // namespace gr
