@@ -36,13 +36,20 @@
 
 namespace gr {
 
-constexpr int BAND_CW = 15;                        // consumer warps
-constexpr int BAND_THREADS = (BAND_CW + 1) * 32;   // + the producer warp (4 warps per SM sub-partition)
-constexpr int BAND_CT = BAND_CW * 32;              // consumer threads
+// Consumer warps per block: 15 (with the producer, four warps per SM
+// sub-partition and 128 registers a thread), or 16 for FP32 blocks of 24
+// columns, where a 17th warp still fits the 96 registers the kernel needs and
+// the larger band fits 224 KB (measured: 117 against 122 us per sweep on the
+// 128^3 mesh; the other shapes ran slower with 16)
+template <typename T, int K>
+__host__ __device__ constexpr int band_cw() { return sizeof(T) == 4 && K == 24 ? 16 : 15; }
+template <typename T, int K>
+__host__ __device__ constexpr int band_threads() { return (band_cw<T, K>() + 1) * 32; }
+template <typename T, int K>
+__host__ __device__ constexpr int band_smem_max() { return (band_cw<T, K>() == 16 ? 224 : 216) * 1024; }
 constexpr int BAND_NS = 3;                         // stages in flight
 constexpr int BAND_CB = 8;                         // consecutive bands per chunk
 constexpr long long BAND_WAIT_CYCLES = 2000000000ll;  // ~1 s at 2 GHz
-constexpr int BAND_SMEM_MAX = 216 * 1024;          // dynamic shared memory budget
 
 // ---------------------------------------------------------------------------
 // Asynchronous copies and mbarriers (PTX)
@@ -373,7 +380,8 @@ __device__ __forceinline__ void band_group(const unsigned char* sl, const unsign
 }
 
 template <typename T, int K>
-__global__ void __launch_bounds__(BAND_THREADS, 1) k_sweep_band(const __grid_constant__ BandArgs<T> a) {
+__global__ void __launch_bounds__(band_threads<T, K>(), 1) k_sweep_band(const __grid_constant__ BandArgs<T> a) {
+    constexpr int BAND_CW = band_cw<T, K>(), BAND_CT = BAND_CW * 32;
     using L = RowLayout<T, K>;
     using Acc = typename AccOf<T>::type;
     constexpr int E = L::E, G = L::G, RB = L::RB;
@@ -643,6 +651,7 @@ static bool band_plan(const gr_ctx* c, bool forced, BandPlan* bp) {
     for (int hh = h; hh >= (forced ? 0 : h); --hh)
         for (int P = 16; P >= 1; --P) {
             const int H = 1 << hh;
+            constexpr int BAND_CW = band_cw<T, K>(), BAND_SMEM_MAX = band_smem_max<T, K>();
             const int R = P * BAND_CW * RPW;  // whole passes of the consumer warps
             if (R & 1) continue;              // row pointers copied in 16-byte units
             const int Rn = (int64_t)R < c->n ? R : (int)c->n;
@@ -828,7 +837,7 @@ static cudaError_t band_launch(gr_ctx* c, const BandPlan& bp, const int4* runs, 
     if (bp.grid > part_cap) return cudaErrorInvalidValue;
     auto kern = k_sweep_band<T, K>;
     GR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bp.smem));
-    kern<<<bp.grid, BAND_THREADS, bp.smem, c->stream>>>(a);
+    kern<<<bp.grid, band_threads<T, K>(), bp.smem, c->stream>>>(a);
     count_launch();
     return cudaGetLastError();
 }
