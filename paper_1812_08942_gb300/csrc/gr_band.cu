@@ -18,8 +18,8 @@
 // Three stages are in flight.  Where each slot's neighbour will sit in shared
 // memory depends only on the plan and the grid, so a per-plan pass stores it
 // in the slot in place of the column (-(column + 1) when it is read from
-// global memory); fifteen consumer warps then gather every neighbour with one
-// shared-memory load and turn the band into output rows.
+// global memory); the consumer warps (band_cw: 15 or 16) then gather every
+// neighbour with one shared-memory load and turn the band into output rows.
 //
 // Products are added in slot order exactly as in the row-group kernel, so the
 // sweep result equals that kernel's given the same statistics.  Every wait is
