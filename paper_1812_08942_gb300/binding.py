@@ -262,13 +262,23 @@ def graph_reduce_coarsen(g: Graph, agg, nc) -> Graph:
     return Graph(h.value, n.value, m.value, g.device)
 
 
-def graph_reduce_get_edges(g: Graph, on_host=False):
-    """Canonical edge list (u, v, w) as tensors (device unless on_host)."""
-    dev = torch.device("cpu") if on_host else g.device
-    kw = {"pin_memory": True} if on_host else {}
-    u = torch.empty(g.m, dtype=torch.int32, device=dev, **kw)
-    v = torch.empty(g.m, dtype=torch.int32, device=dev, **kw)
-    w = torch.empty(g.m, dtype=torch.float64, device=dev, **kw)
+def graph_reduce_get_edges(g: Graph, on_host=False, out=None):
+    """Canonical edge list (u, v, w) as tensors (device unless on_host).  out:
+    optional (u, v, w) tensors to fill (m entries each, int32 / int32 /
+    float64, on the host -- pinned for a fast copy -- or on g's device as
+    on_host says), e.g. buffers a caller reuses across graphs."""
+    if out is not None:
+        u, v, w = out
+        assert u.numel() >= g.m and v.numel() >= g.m and w.numel() >= g.m
+        assert u.dtype == torch.int32 and v.dtype == torch.int32 and w.dtype == torch.float64
+        assert all(t.is_cuda != bool(on_host) and t.is_contiguous() for t in (u, v, w))
+        u, v, w = u[:g.m], v[:g.m], w[:g.m]
+    else:
+        dev = torch.device("cpu") if on_host else g.device
+        kw = {"pin_memory": True} if on_host else {}
+        u = torch.empty(g.m, dtype=torch.int32, device=dev, **kw)
+        v = torch.empty(g.m, dtype=torch.int32, device=dev, **kw)
+        w = torch.empty(g.m, dtype=torch.float64, device=dev, **kw)
     m = ctypes.c_int64()
     st = load().graph_reduce_get_edges(g.handle, ctypes.byref(m), _ptr(u), _ptr(v), _ptr(w), 1 if on_host else 0)
     _check(st, g.handle)

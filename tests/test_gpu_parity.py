@@ -62,6 +62,17 @@ def test_create_roundtrip_and_validation(gr, oracle_mod):
                                 torch.from_numpy(g.w).to(DEV))
     u2, _, _ = gr.graph_reduce_get_edges(G2)
     assert torch.equal(u2.cpu(), torch.from_numpy(g.u))
+    # caller-provided outputs, larger than needed: pinned host and device
+    for on_host in (True, False):
+        kw = {"device": DEV} if not on_host else {}
+        out = (torch.full((g.m + 5,), -1, dtype=torch.int32, **kw), torch.full((g.m + 5,), -1, dtype=torch.int32, **kw),
+               torch.zeros(g.m + 5, dtype=torch.float64, **kw))
+        if on_host:
+            out = tuple(t.pin_memory() for t in out)
+        u3, v3, w3 = gr.graph_reduce_get_edges(G2, on_host=on_host, out=out)
+        torch.cuda.synchronize()
+        assert u3.numel() == g.m and np.array_equal(u3.cpu().numpy(), g.u) and np.array_equal(v3.cpu().numpy(), g.v)
+        assert np.array_equal(w3.cpu().numpy(), g.w) and int(out[0][g.m].item()) == -1
     bad = [
         (g.v, g.u, g.w),                                   # u > v
         (g.u[::-1].copy(), g.v[::-1].copy(), g.w),         # unsorted
