@@ -130,13 +130,15 @@ gr_status graph_reduce_smooth_noalloc(gr_ctx* ctx, int K, int sweeps, double ome
  * slot order, so they agree within the rounding of the column statistics.
  *   GR_SWEEP_AUTO    (default) the streaming kernel when rows are long (a
  *                    warp's group of 32 / lanes-per-row rows would hold over
- *                    128 slots); else the band kernel when the graph is in a
- *                    banded order: at least half of its slots within a halo
- *                    of at most 1,024 rows that fits shared memory, and at
- *                    least 95 % of the neighbours held in shared memory by
- *                    the band tables (measured once per context and plan:
- *                    two stream synchronisations; tables of a graph that
- *                    fails are freed); else the row-group kernel
+ *                    128 slots); else the band kernel when the graph has at
+ *                    least 640 rows per SM (enough for a chunk of bands on
+ *                    every SM) and is in a banded order: at least half of
+ *                    its slots within a halo of at most 1,024 rows that fits
+ *                    shared memory, and at least 95 % of the neighbours held
+ *                    in shared memory by the band tables (measured once per
+ *                    context and plan: two stream synchronisations; tables
+ *                    of a graph that fails are freed); else the row-group
+ *                    kernel
  *   GR_SWEEP_ROW     row-group kernel: one lane per 16-byte chunk of a vector
  *                    row, several rows per warp, rows grid-strided
  *   GR_SWEEP_STREAM  warp per row over a slot-balanced row partition, the

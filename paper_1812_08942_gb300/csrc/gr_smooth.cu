@@ -665,9 +665,10 @@ static cudaError_t prepare_stream(gr_ctx* c, SweepScratch& sc, int part_cap, Swe
 
 // Band kernel: when forced, wherever a band fits shared memory; in the
 // automatic choice, for rows that are not long (the streaming kernel's case)
-// on graphs whose locality profile admits a band and whose tables place at
-// least BAND_AUTO_SHARED of the neighbours in shared memory (the verdict is
-// kept in the context per plan).  `tmp` (at least 264 bytes of device memory
+// on graphs large enough to give every SM a chunk of bands (smaller ones skip
+// the locality profile and its synchronisation), whose locality profile
+// admits a band and whose tables place at least BAND_AUTO_SHARED of the
+// neighbours in shared memory (the verdict is kept in the context per plan).  `tmp` (at least 264 bytes of device memory
 // the stream does not use yet) holds the locality profile's counts on the
 // first call.  *chosen tells whether P now runs the band kernel.
 constexpr double BAND_AUTO_SHARED = 0.95;
@@ -678,9 +679,13 @@ static cudaError_t choose_band(gr_ctx* c, SweepScratch& sc, void* tmp, SweepPlan
     const int want = c->sweep_kind;
     constexpr bool f64 = sizeof(T) == 8;
     if (want != GR_SWEEP_BAND && !(want == GR_SWEEP_AUTO && !stream_wide<T, K>(c))) return cudaSuccess;
+    // FP32 / BF16 bands hold 80 rows or more and a chunk 8 bands: smaller
+    // graphs could not give every SM a chunk
+    if (want == GR_SWEEP_AUTO && c->n < (int64_t)c->num_sms * 8 * 80) return cudaSuccess;
     GR_CUDA(ensure_locality(c, tmp));
     BandPlan bp;
     if (!band_usable(c, prec_of<T>(), K, want == GR_SWEEP_BAND, &bp)) return cudaSuccess;
+    if (want == GR_SWEEP_AUTO && bp.grid < c->num_sms) return cudaSuccess;
     const bool known = c->band_auto_ok >= 0 && c->band_auto_R == bp.R && c->band_auto_H == bp.H &&
                        c->band_auto_grid == bp.grid && c->band_auto_f64 == (int)f64;
     if (want == GR_SWEEP_AUTO && known && c->band_auto_ok == 0) return cudaSuccess;

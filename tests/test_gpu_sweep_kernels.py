@@ -1,8 +1,8 @@
 """GPU parity of the sweep kernels (Alg. 3 weighted-Jacobi sweeps, Sec.
 3.2.1) against the FP64 oracle: each kernel is forced on each graph family
 through graph_reduce_set_sweep_kernel, and the automatic choice is checked
-(band kernel on the grids and the path, not where random long edges or a hub
-scatter the neighbours).
+(band kernel on a banded grid large enough to fill the GPU, not on smaller
+graphs nor where random long edges scatter the neighbours).
 The band kernel fits shared memory on every family and size here, so forcing
 it runs it; its neighbours come from the window ring, the far runs and global
 memory (random long edges, the hub's row past a stage's slot capacity).
@@ -75,10 +75,10 @@ FAMILIES = {
 }
 
 KINDS = ["ROW", "STREAM", "BAND", "AUTO"]
-# the automatic choice: banded orders get the band kernel, scattered ones not
-# (the 300-node star fits one band window whole, so either is right there)
-AUTO_BAND = ("grid64", "grid160x120", "path_iso")
-AUTO_NOT_BAND = ("rand_w", "grid_long_hub")
+# the automatic choice leaves the band kernel to graphs large enough to give
+# every SM a chunk of bands (test_auto_band_on_a_large_grid); these families
+# are all smaller
+AUTO_NOT_BAND = tuple(FAMILIES)
 
 
 def _kind(gr, name):
@@ -105,10 +105,7 @@ def test_sweep_kernels_f64_f32(gr, oracle_mod, kind, name):
             if kind != "AUTO":
                 assert plan == _kind(gr, kind)
             elif name in AUTO_NOT_BAND:
-                # neighbours scattered (random edges, a hub): not the band kernel
                 assert plan != gr.GR_SWEEP_BAND, (K, plan)
-            elif name in AUTO_BAND and dtype == torch.float32 and K == 16:
-                assert plan == gr.GR_SWEEP_BAND, (K, plan)
             X = _smooth(gr, G, g.n, K, dtype, S, omega, seed, level)
             err = _col_relerr(X.double().cpu().numpy(), ref).max()
             assert err <= bar, (name, kind, K, dtype, err, plan)
@@ -128,6 +125,27 @@ def test_sweep_kernels_large_grid(gr, oracle_mod, kind, K):
         X = _smooth(gr, G, g.n, K, dtype, S, omega, seed, level)
         err = _col_relerr(X.double().cpu().numpy(), ref).max()
         assert err <= bar, (kind, K, dtype, err)
+
+
+@pytest.mark.parametrize("K", [16, 24])
+def test_auto_band_on_a_large_grid(gr, oracle_mod, K):
+    # 200 x 1100 grid (220,000 nodes, rows 200 apart): large enough for a
+    # chunk of bands per SM and banded, so the automatic choice takes the band
+    # kernel; a grid with random long edges of the same size does not
+    g = W.grid2d(200, 1100, weights=lambda m: np.random.default_rng(7).lognormal(0.0, 0.5, m))
+    G = gr.graph_reduce_create(g.n, g.u, g.v, g.w)
+    S, omega, seed, level = 5, 0.7, 3, 0
+    ref = oracle_mod.smooth(g.n, g.u, g.v, g.w, K, S, omega, seed, level)
+    for dtype, bar in ((torch.float64, 1e-12), (torch.float32, 1e-5)):
+        plan = gr.graph_reduce_sweep_plan(G, K, dtype)
+        if dtype == torch.float32:
+            assert plan == gr.GR_SWEEP_BAND, plan
+        X = _smooth(gr, G, g.n, K, dtype, S, omega, seed, level)
+        err = _col_relerr(X.double().cpu().numpy(), ref).max()
+        assert err <= bar, (K, dtype, err, plan)
+    h = _grid_plus(200, 1100, 60000, 100, seed=5)
+    H = gr.graph_reduce_create(h.n, h.u, h.v, h.w)
+    assert gr.graph_reduce_sweep_plan(H, K, torch.float32) != gr.GR_SWEEP_BAND
 
 
 def test_sweep_kernels_bf16_agree(gr):

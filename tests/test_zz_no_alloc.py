@@ -33,7 +33,7 @@ def gr():
 
 GRAPHS = {
     "random": lambda: W.random_sparse(20011, 90000, seed=17),
-    "grid": lambda: W.grid2d(160, 125),  # banded: the automatic choice takes the band kernel
+    "grid": lambda: W.grid2d(200, 1100),  # banded and large: the automatic choice takes the band kernel
 }
 
 
