@@ -275,8 +275,11 @@ __global__ void k_offset_hist(int64_t n, const int64_t* __restrict__ rowptr, con
         const int64_t b = rowptr[r], e = rowptr[r + 1];
         for (int64_t j = b; j < e; ++j) {
             const int64_t d = llabs((int64_t)col[j] - r);
-            const int bk = d <= 1 ? 0 : 64 - __clzll((long long)(d - 1));
-            atomicAdd(&sh[bk < 32 ? bk : 32], 1u);
+            const int bk0 = d <= 1 ? 0 : 64 - __clzll((long long)(d - 1));
+            const int bk = bk0 < 32 ? bk0 : 32;
+            // one shared atomic per bucket among the lanes here together
+            const unsigned peers = __match_any_sync(__activemask(), bk);
+            if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&sh[bk], (unsigned)__popc(peers));
         }
     }
     __syncthreads();

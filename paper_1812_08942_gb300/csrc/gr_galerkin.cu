@@ -91,18 +91,19 @@ __global__ void k_gal_scatter(const int32_t* __restrict__ agg, const int64_t* __
     }
 }
 
-// ascending bitonic sort of P (power of two) keys in shared memory by one warp
+// ascending bitonic sort of P (power of two, at least 64) keys in shared
+// memory by one warp; the lanes take the stage's P / 2 compare-exchange
+// pairs (t, t + j), t with bit j clear, so none idles
 __device__ __forceinline__ void warp_bitonic(uint64_t* K, int P, int lane) {
     for (int k = 2; k <= P; k <<= 1)
         for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int t = lane; t < P; t += 32) {
-                const int u = t ^ j;
-                if (u > t) {
-                    const uint64_t a = K[t], b = K[u];
-                    if ((a > b) == ((t & k) == 0)) {
-                        K[t] = b;
-                        K[u] = a;
-                    }
+            for (int p = lane; p < (P >> 1); p += 32) {
+                const int t = ((p & ~(j - 1)) << 1) | (p & (j - 1));
+                const int u = t | j;
+                const uint64_t a = K[t], b = K[u];
+                if ((a > b) == ((t & k) == 0)) {
+                    K[t] = b;
+                    K[u] = a;
                 }
             }
             __syncwarp();

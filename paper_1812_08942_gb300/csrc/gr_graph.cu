@@ -171,21 +171,118 @@ __global__ void k_lower_claim(const int32_t* __restrict__ ev, int64_t m, const i
 // thread per row (graphs of mean degree below 32): insertion-sort the lower ids, write
 // the row, D(p,p) summed sequentially in slot order (= ascending edge id),
 // then w / D(p,p).  Rows with longer lower parts go to the warp kernel's list.
-__global__ void k_row_finish_thread(int64_t n, const int64_t* __restrict__ rowptr, const int64_t* __restrict__ eptr,
-                                    const int32_t* __restrict__ lcnt, const int32_t* __restrict__ eu,
-                                    const int32_t* __restrict__ ev, const double* __restrict__ ew,
-                                    int32_t* __restrict__ col, int32_t* __restrict__ eid,
-                                    double* __restrict__ wn64, int2* __restrict__ cw32, double* __restrict__ deg,
-                                    int32_t* __restrict__ list, int32_t* __restrict__ nlist) {
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n) return;
-    const int L = lcnt[p];
-    const int32_t k = warp_slot(L > LOWER_THREAD, nlist);
-    if (k >= 0) {
-        list[k] = (int32_t)p;
+//
+// A warp's 32 rows are consecutive, so their slots and their upper edges are
+// two contiguous ranges.  When both fit the warp's shared-memory buffers (and
+// no row of the warp is listed), the warp reads the claimed lower ids and the
+// upper edges' ends and weights in whole lines, each thread builds its row in
+// the buffers, and the warp writes the four slot arrays in whole lines; only
+// the lower edges' own ends and weights are gathered.  Other warps write each
+// row from its thread (the same values in the same order).
+constexpr int FIN_CAP = 256;   // slots a warp stages
+constexpr int FIN_ECAP = 160;  // upper edges a warp stages
+
+__global__ void __launch_bounds__(TB, 4) k_row_finish_thread(int64_t n, const int64_t* __restrict__ rowptr,
+                                                          const int64_t* __restrict__ eptr,
+                                                          const int32_t* __restrict__ lcnt,
+                                                          const int32_t* __restrict__ eu,
+                                                          const int32_t* __restrict__ ev,
+                                                          const double* __restrict__ ew, int32_t* __restrict__ col,
+                                                          int32_t* __restrict__ eid, double* __restrict__ wn64,
+                                                          int2* __restrict__ cw32, double* __restrict__ deg,
+                                                          int32_t* __restrict__ list, int32_t* __restrict__ nlist) {
+    __shared__ int32_t s_col[TB / 32][FIN_CAP];
+    __shared__ int32_t s_eid[TB / 32][FIN_CAP];
+    __shared__ double s_w[TB / 32][FIN_CAP];
+    __shared__ int32_t s_ev[TB / 32][FIN_ECAP];
+    __shared__ double s_ew[TB / 32][FIN_ECAP];
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const int64_t pw = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31);  // the warp's first row
+    if (pw >= n) return;                                                       // whole warp
+    const int64_t p = pw + lane;
+    const bool in = p < n;
+    const int L = in ? lcnt[p] : 0;
+    const bool listed = L > LOWER_THREAD;
+    const int32_t k = warp_slot(listed, nlist);
+    if (k >= 0) list[k] = (int32_t)p;
+    int64_t r0 = 0, e0 = 0, e1 = 0;
+    if (in) {
+        r0 = rowptr[p];
+        e0 = eptr[p];
+        e1 = eptr[p + 1];
+    }
+    const int lv = (int)((n - pw < 32 ? n - pw : 32) - 1);  // the warp's last row
+    const int64_t R0 = __shfl_sync(FULL, r0, 0), E0 = __shfl_sync(FULL, e0, 0);
+    const int64_t E1 = __shfl_sync(FULL, e1, lv);
+    const int64_t R1 = __shfl_sync(FULL, r0 + L + (e1 - e0), lv);
+    const bool staged = !__any_sync(FULL, listed) && R1 - R0 <= FIN_CAP && E1 - E0 <= FIN_ECAP;
+    if (staged) {
+        int32_t* S_col = s_col[wp];
+        int32_t* S_eid = s_eid[wp];
+        double* S_w = s_w[wp];
+        int32_t* S_ev = s_ev[wp];
+        double* S_ew = s_ew[wp];
+        const int ns = (int)(R1 - R0), ne = (int)(E1 - E0);
+        for (int j = lane; j < ns; j += 32) S_eid[j] = eid[R0 + j];  // lower parts: ids in claim order
+        for (int j = lane; j < ne; j += 32) {
+            S_ev[j] = ev[E0 + j];
+            S_ew[j] = ew[E0 + j];
+        }
+        __syncwarp();
+        if (in) {
+            const int b = (int)(r0 - R0), u0 = (int)(e0 - E0), U = (int)(e1 - e0);
+            for (int i = 1; i < L; ++i) {
+                const int32_t x = S_eid[b + i];
+                int j = i;
+                while (j > 0 && S_eid[b + j - 1] > x) {
+                    S_eid[b + j] = S_eid[b + j - 1];
+                    --j;
+                }
+                S_eid[b + j] = x;
+            }
+            double sum = 0.0;
+            for (int i0 = 0; i0 < L; i0 += 4) {  // four lower edges' ends and weights in flight
+                int32_t e4[4], c4[4];
+                double w4[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+                    if (i0 + t < L) {
+                        e4[t] = S_eid[b + i0 + t];
+                        w4[t] = ew[e4[t]];
+                        c4[t] = eu[e4[t]];
+                    }
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+                    if (i0 + t < L) {
+                        S_col[b + i0 + t] = c4[t];
+                        S_w[b + i0 + t] = w4[t];
+                        sum += w4[t];
+                    }
+            }
+            for (int i = 0; i < U; ++i) {
+                const double w = S_ew[u0 + i];
+                S_col[b + L + i] = S_ev[u0 + i];
+                S_eid[b + L + i] = (int32_t)(e0 + i);
+                S_w[b + L + i] = w;
+                sum += w;
+            }
+            deg[p] = sum;
+            const double inv = sum > 0.0 ? 1.0 / sum : 0.0;
+            for (int i = 0; i < L + U; ++i) S_w[b + i] = S_w[b + i] * inv;
+        }
+        __syncwarp();
+        for (int j = lane; j < ns; j += 32) {
+            const int32_t cj = S_col[j];
+            const double x = S_w[j];
+            col[R0 + j] = cj;
+            eid[R0 + j] = S_eid[j];
+            wn64[R0 + j] = x;
+            cw32[R0 + j] = make_int2(cj, __float_as_int((float)x));
+        }
         return;
     }
-    const int64_t r0 = rowptr[p], e0 = eptr[p], e1 = eptr[p + 1];
+    if (!in || listed) return;
     int32_t le[LOWER_THREAD];
     for (int i = 0; i < L; ++i) {
         const int32_t x = eid[r0 + i];
