@@ -98,11 +98,49 @@ __global__ void k_degree_scale(const int64_t* __restrict__ rowptr, const int32_t
 }
 
 // thread per row (short rows): D(p,p) summed sequentially in slot order,
-// which is ascending edge id -- the plain definition's order
-__global__ void k_degree_scale_rows(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                                    int64_t n, double* __restrict__ wn64, int2* __restrict__ cw32,
-                                    double* __restrict__ deg) {
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// which is ascending edge id -- the plain definition's order.  A warp's 32
+// rows are consecutive: when their slots fit the warp's shared-memory buffer
+// the warp reads the weights and columns in whole lines, each thread sums and
+// scales its row there, and the warp writes both slot arrays in whole lines.
+constexpr int DS_CAP = 512;  // slots a warp stages
+
+__global__ void __launch_bounds__(TB, 4) k_degree_scale_rows(const int64_t* __restrict__ rowptr,
+                                                          const int32_t* __restrict__ col, int64_t n,
+                                                          double* __restrict__ wn64, int2* __restrict__ cw32,
+                                                          double* __restrict__ deg) {
+    __shared__ double s_w[TB / 32][DS_CAP];
+    __shared__ int32_t s_c[TB / 32][DS_CAP];
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const int64_t pw = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31);
+    if (pw >= n) return;  // whole warp
+    const int64_t p = pw + lane;
+    const int lv = (int)((n - pw < 32 ? n - pw : 32) - 1);
+    const int64_t R0 = rowptr[pw], R1 = rowptr[pw + lv + 1];
+    if (R1 - R0 <= DS_CAP) {
+        double* W = s_w[wp];
+        int32_t* C = s_c[wp];
+        const int ns = (int)(R1 - R0);
+        for (int j = lane; j < ns; j += 32) {
+            W[j] = wn64[R0 + j];
+            C[j] = col[R0 + j];
+        }
+        __syncwarp();
+        if (p < n) {
+            const int b = (int)(rowptr[p] - R0), e = (int)(rowptr[p + 1] - R0);
+            double s = 0.0;
+            for (int j = b; j < e; ++j) s += W[j];
+            deg[p] = s;
+            const double inv = s > 0.0 ? 1.0 / s : 0.0;
+            for (int j = b; j < e; ++j) W[j] = W[j] * inv;
+        }
+        __syncwarp();
+        for (int j = lane; j < ns; j += 32) {
+            const double x = W[j];
+            wn64[R0 + j] = x;
+            cw32[R0 + j] = make_int2(C[j], __float_as_int((float)x));
+        }
+        return;
+    }
     if (p >= n) return;
     const int64_t b = rowptr[p], e = rowptr[p + 1];
     double s = 0.0;

@@ -231,15 +231,26 @@ __device__ __forceinline__ int32_t warp_slot(bool keep, int32_t* count) {
 }
 
 // kernels entry points used by the API layer
-// ev_begin / ev_end (optional) are recorded around the sweep kernels only
+// ev_begin / ev_end (optional) are recorded around the sweep kernels only.
+// raw (optional): the last normalisation X = (A - mu) / s is left to the
+// caller, who gets the block A (X itself or a workspace buffer of c) and its
+// statistics (mu[K] then 1/s[K], FP64, workspace of c) -- valid until c's
+// next smoothing call.
+struct SmoothRaw {
+    const void* A;
+    const double* stats;
+};
 gr_status test_vectors_impl(gr_ctx* c, int K, uint64_t seed, int level, gr_prec prec, void* X);
 gr_status smooth_impl(gr_ctx* c, int K, int sweeps, double omega, uint64_t seed, int level,
                       gr_prec prec, void* X, cudaEvent_t ev_begin = nullptr,
-                      cudaEvent_t ev_end = nullptr);
+                      cudaEvent_t ev_end = nullptr, SmoothRaw* raw = nullptr);
 gr_status smooth_gs_impl(gr_ctx* c, int K, int sweeps, double omega, uint64_t seed, int level,
                          uint64_t colour_seed, gr_prec prec, void* X);
 gr_status colour_impl(gr_ctx* c, uint64_t colour_seed, int32_t* colour_out, int32_t* ncolours_out);
-gr_status affinity_impl(gr_ctx* c, const void* X, int K, gr_prec prec, void* d, void* a);
+// stats (optional): X is a block still to be normalised by these column
+// statistics (the layout of SmoothRaw), rounded as the stored block would be
+gr_status affinity_impl(gr_ctx* c, const void* X, int K, gr_prec prec, void* d, void* a,
+                        const double* stats = nullptr);
 gr_status aggregate_impl(gr_ctx* c, const void* d, int d_is_f64, int64_t target_nc, int passes,
                          int64_t max_proposals, int32_t* agg, int64_t* nc_out, int64_t* proposals_out);
 gr_status coarsen_impl(gr_ctx* c, const int32_t* agg, int64_t nc, gr_ctx** out);

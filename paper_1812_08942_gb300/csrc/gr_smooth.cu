@@ -796,7 +796,7 @@ constexpr size_t stats_bytes() {
 template <typename T, int K>
 static cudaError_t run_sweeps(gr_ctx* c, SweepScratch& sc, int sweeps, double omega, uint64_t seed, int level,
                               T* X, T* buf, double* stats, double* part, int part_cap, cudaEvent_t ev0,
-                              cudaEvent_t ev1) {
+                              cudaEvent_t ev1, SmoothRaw* raw = nullptr) {
     cudaStream_t s = c->stream;
     const int64_t n = c->n;
     double* st0 = stats;
@@ -825,6 +825,11 @@ static cudaError_t run_sweeps(gr_ctx* c, SweepScratch& sc, int sweeps, double om
         sout = ts;
     }
     if (ev1) GR_CUDA(cudaEventRecord(ev1, s));
+    if (raw) {  // the caller applies the statistics
+        raw->A = cur;
+        raw->stats = sin;
+        return cudaSuccess;
+    }
     constexpr int G = RowLayout<T, K>::G;
     if (n > 0) {
         k_apply<T, K><<<(unsigned)ceil_div(n * G, 256), 256, 0, s>>>(n, cur, X, sin);
@@ -838,7 +843,7 @@ static int part_capacity(const gr_ctx* c) { return c->num_sms * 8; }
 
 template <typename T, int K>
 static cudaError_t run_smooth(gr_ctx* c, int sweeps, double omega, uint64_t seed, int level,
-                              T* X, cudaEvent_t ev0, cudaEvent_t ev1) {
+                              T* X, cudaEvent_t ev0, cudaEvent_t ev1, SmoothRaw* raw) {
     const int64_t n = c->n;
     void *p_buf, *p_st, *p_part;
     const int cap = part_capacity(c);
@@ -847,18 +852,18 @@ static cudaError_t run_smooth(gr_ctx* c, int sweeps, double omega, uint64_t seed
     GR_CUDA(c->ws.get(WS_SMOOTH_PART, sizeof(double) * 2 * K * (size_t)cap, &p_part));
     SweepScratch sc;
     return run_sweeps<T, K>(c, sc, sweeps, omega, seed, level, X, (T*)p_buf, (double*)p_st, (double*)p_part, cap,
-                            ev0, ev1);
+                            ev0, ev1, raw);
 }
 
 template <typename T>
 static cudaError_t smooth_typed(gr_ctx* c, int K, int sweeps, double omega, uint64_t seed,
-                                int level, void* X, cudaEvent_t e0, cudaEvent_t e1) {
+                                int level, void* X, cudaEvent_t e0, cudaEvent_t e1, SmoothRaw* raw) {
     switch (K) {
-        case 4: return run_smooth<T, 4>(c, sweeps, omega, seed, level, (T*)X, e0, e1);
-        case 8: return run_smooth<T, 8>(c, sweeps, omega, seed, level, (T*)X, e0, e1);
-        case 16: return run_smooth<T, 16>(c, sweeps, omega, seed, level, (T*)X, e0, e1);
-        case 24: return run_smooth<T, 24>(c, sweeps, omega, seed, level, (T*)X, e0, e1);
-        case 32: return run_smooth<T, 32>(c, sweeps, omega, seed, level, (T*)X, e0, e1);
+        case 4: return run_smooth<T, 4>(c, sweeps, omega, seed, level, (T*)X, e0, e1, raw);
+        case 8: return run_smooth<T, 8>(c, sweeps, omega, seed, level, (T*)X, e0, e1, raw);
+        case 16: return run_smooth<T, 16>(c, sweeps, omega, seed, level, (T*)X, e0, e1, raw);
+        case 24: return run_smooth<T, 24>(c, sweeps, omega, seed, level, (T*)X, e0, e1, raw);
+        case 32: return run_smooth<T, 32>(c, sweeps, omega, seed, level, (T*)X, e0, e1, raw);
     }
     return cudaErrorInvalidValue;
 }
@@ -906,12 +911,12 @@ gr_status test_vectors_impl(gr_ctx* c, int K, uint64_t seed, int level, gr_prec 
 }
 
 gr_status smooth_impl(gr_ctx* c, int K, int sweeps, double omega, uint64_t seed, int level,
-                      gr_prec prec, void* X, cudaEvent_t e0, cudaEvent_t e1) {
+                      gr_prec prec, void* X, cudaEvent_t e0, cudaEvent_t e1, SmoothRaw* raw) {
     cudaError_t e;
     switch (prec) {
-        case GR_F64: e = smooth_typed<double>(c, K, sweeps, omega, seed, level, X, e0, e1); break;
-        case GR_F32: e = smooth_typed<float>(c, K, sweeps, omega, seed, level, X, e0, e1); break;
-        case GR_BF16: e = smooth_typed<__nv_bfloat16>(c, K, sweeps, omega, seed, level, X, e0, e1); break;
+        case GR_F64: e = smooth_typed<double>(c, K, sweeps, omega, seed, level, X, e0, e1, raw); break;
+        case GR_F32: e = smooth_typed<float>(c, K, sweeps, omega, seed, level, X, e0, e1, raw); break;
+        case GR_BF16: e = smooth_typed<__nv_bfloat16>(c, K, sweeps, omega, seed, level, X, e0, e1, raw); break;
         default: return set_error(c, GR_EINVAL, "smooth: unknown precision");
     }
     if (e != cudaSuccess) return cuda_error(c, e, "smooth");

@@ -476,6 +476,36 @@ def test_multilevel_f64_eigs(gr, oracle_mod, shape, final):
     assert all(s["proposals"] > 0 for s in stats)
 
 
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32, torch.bfloat16])
+@pytest.mark.parametrize("S", [4, 5])
+@pytest.mark.parametrize("name", ["grid160x120", "rand_w", "dense_rand"])
+def test_multilevel_equals_the_calls_it_chains(gr, name, S, dtype):
+    # on sparse graphs the level loop hands the smoothed block to the
+    # affinity unnormalised (the affinity applies the last normalisation;
+    # dense_rand, of mean degree 39, keeps the separate pass): its first two
+    # levels must equal smoothing, affinity, aggregation and coarsening called
+    # one by one, bit for bit, for every storage type and sweep-count parity
+    g = W.grid2d(160, 120) if name == "grid160x120" else GRAPHS[name]()
+    K, seed, ratio = 16, 7, 4
+    prec = {torch.float64: gr.GR_F64, torch.float32: gr.GR_F32, torch.bfloat16: gr.GR_BF16}[dtype]
+    G = gr.graph_reduce_create(g.n, g.u, g.v, g.w)
+    p = gr.ReduceParams(K=K, sweeps=S, seed=seed, prec=prec, level_ratio=ratio, final_target=8, max_levels=2)
+    glev, _ = gr.graph_reduce_multilevel(G, p)
+    assert len(glev) == 2
+    cur = gr.graph_reduce_create(g.n, g.u, g.v, g.w)
+    for lvl in range(2):
+        X = torch.empty(cur.n, K, dtype=dtype, device=DEV)
+        gr.graph_reduce_smooth(cur, X, S, 0.7, seed, lvl)
+        d = torch.empty(cur.m, dtype=torch.float64 if dtype == torch.float64 else torch.float32, device=DEV)
+        gr.graph_reduce_affinity(cur, X, d)
+        agg, nc, _ = gr.graph_reduce_aggregate(cur, d, max((cur.n + ratio - 1) // ratio, 8))
+        nxt = gr.graph_reduce_coarsen(cur, agg, nc)
+        assert torch.equal(gr.graph_reduce_get_map(glev[lvl]), agg), lvl
+        for a, b in zip(gr.graph_reduce_get_edges(glev[lvl]), gr.graph_reduce_get_edges(nxt)):
+            assert torch.equal(a, b), lvl
+        cur = nxt
+
+
 # ---------------------------------------------------------------------------
 # spectral-mismatch loss and its adjoint
 # ---------------------------------------------------------------------------
