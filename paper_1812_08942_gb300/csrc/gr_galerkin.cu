@@ -91,6 +91,61 @@ __global__ void k_gal_scatter(const int32_t* __restrict__ agg, const int64_t* __
     }
 }
 
+// Each fine node's slots into its aggregate's key segment, a warp per 32
+// consecutive nodes: each lane claims its node's place in the segment, then
+// the warp runs over the nodes' slots -- one contiguous range -- a slot per
+// lane, so the column and edge-id reads come in whole lines.  Ranges longer
+// than SC_CAP slots are written by each node's own lane.
+constexpr int SC_CAP = 1024;
+
+__global__ void __launch_bounds__(GT) k_gal_scatter_warp(const int32_t* __restrict__ agg,
+                                                         const int64_t* __restrict__ rowptr,
+                                                         const int32_t* __restrict__ col,
+                                                         const int32_t* __restrict__ eid, int64_t n,
+                                                         const int64_t* __restrict__ sptr,
+                                                         unsigned long long* __restrict__ sfill,
+                                                         uint64_t* __restrict__ keys) {
+    __shared__ uint8_t s_row[GT / 32][SC_CAP];
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const int64_t pw = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31);
+    if (pw >= n) return;  // whole warp
+    const int64_t p = pw + lane;
+    const bool in = p < n;
+    const int32_t a = in ? agg[p] : 0;
+    const int64_t b0 = in ? rowptr[p] : 0;
+    const int64_t len = in ? rowptr[p + 1] - b0 : 0;
+    int64_t off = 0;
+    if (len) off = sptr[a] + (int64_t)atomicAdd(&sfill[a], (unsigned long long)len);
+    const int lv = (int)((n - pw < 32 ? n - pw : 32) - 1);
+    const int64_t R0 = __shfl_sync(FULL, b0, 0);
+    const int64_t R1 = __shfl_sync(FULL, b0 + len, lv);
+    if (R1 - R0 > SC_CAP) {
+        for (int64_t k = 0; k < len; ++k) {
+            const int64_t j = b0 + k;
+            const int32_t B = __ldg(agg + col[j]);
+            keys[off + k] = B == a ? NOKEY : (((uint64_t)(uint32_t)B << 32) | (uint64_t)(uint32_t)eid[j]);
+        }
+        return;
+    }
+    uint8_t* S = s_row[wp];
+    for (int64_t k = 0; k < len; ++k) S[b0 - R0 + k] = (uint8_t)lane;
+    __syncwarp();
+    const int ns = (int)(R1 - R0);
+    for (int j0 = 0; j0 < ns; j0 += 32) {
+        const int j = j0 + lane;
+        const int r = j < ns ? S[j] : 0;
+        const int32_t ar = __shfl_sync(FULL, a, r);
+        const int64_t offr = __shfl_sync(FULL, off, r);
+        const int64_t br = __shfl_sync(FULL, b0, r);
+        if (j < ns) {
+            const int64_t g = R0 + j;
+            const int32_t B = __ldg(agg + col[g]);
+            keys[offr + (g - br)] = B == ar ? NOKEY : (((uint64_t)(uint32_t)B << 32) | (uint64_t)(uint32_t)eid[g]);
+        }
+    }
+}
+
 // ascending bitonic sort of P (power of two, at least 64) keys in shared
 // memory by one warp; the lanes take the stage's P / 2 compare-exchange
 // pairs (t, t + j), t with bit j clear, so none idles
@@ -370,8 +425,8 @@ gr_status galerkin_rows(gr_ctx* c, const int32_t* agg, int64_t nc, gr_ctx* cc, b
             k_gal_scatter<32><<<(unsigned)ceil_div(n * 32, GT), GT, 0, s>>>(agg, c->rowptr, c->col, c->eid, n, sptr,
                                                                            sfill, keys);
         } else {
-            k_gal_scatter<1><<<(unsigned)ceil_div(n, GT), GT, 0, s>>>(agg, c->rowptr, c->col, c->eid, n, sptr, sfill,
-                                                                     keys);
+            k_gal_scatter_warp<<<(unsigned)ceil_div(n, GT), GT, 0, s>>>(agg, c->rowptr, c->col, c->eid, n, sptr,
+                                                                       sfill, keys);
         }
         count_launch();
     }
