@@ -266,20 +266,46 @@ __global__ void k_band_slots(int n, int nbands, int R, int H, int WR, int FC, co
 // ---------------------------------------------------------------------------
 // Locality profile: histogram of |c - r| over all slots in log2 buckets
 // ---------------------------------------------------------------------------
-__global__ void k_offset_hist(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                              unsigned long long* __restrict__ hist) {
+// A warp takes 32 consecutive rows: their slots are one contiguous range,
+// which the lanes run over a slot each (the row of each slot from a
+// shared-memory map); ranges longer than HIST_CAP slots are run row by row.
+constexpr int HIST_CAP = 1024;
+
+__global__ void __launch_bounds__(256) k_offset_hist(int64_t n, const int64_t* __restrict__ rowptr,
+                                                     const int32_t* __restrict__ col,
+                                                     unsigned long long* __restrict__ hist) {
     __shared__ unsigned int sh[33];
+    __shared__ uint8_t s_row[8][HIST_CAP];
+    constexpr unsigned FULL = 0xffffffffu;
     for (int i = threadIdx.x; i < 33; i += blockDim.x) sh[i] = 0u;
     __syncthreads();
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t b = rowptr[r], e = rowptr[r + 1];
-        for (int64_t j = b; j < e; ++j) {
-            const int64_t d = llabs((int64_t)col[j] - r);
-            const int bk0 = d <= 1 ? 0 : 64 - __clzll((long long)(d - 1));
-            const int bk = bk0 < 32 ? bk0 : 32;
-            // one shared atomic per bucket among the lanes here together
-            const unsigned peers = __match_any_sync(__activemask(), bk);
-            if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&sh[bk], (unsigned)__popc(peers));
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    auto bucket = [](int64_t d) {
+        const int bk = d <= 1 ? 0 : 64 - __clzll((long long)(d - 1));
+        return bk < 32 ? bk : 32;
+    };
+    for (int64_t pw = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)); pw < n;
+         pw += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = pw + lane;
+        const bool in = r < n;
+        const int64_t b = in ? rowptr[r] : 0, e = in ? rowptr[r + 1] : 0;
+        const int lv = (int)((n - pw < 32 ? n - pw : 32) - 1);
+        const int64_t R0 = __shfl_sync(FULL, b, 0), R1 = __shfl_sync(FULL, e, lv);
+        if (R1 - R0 <= HIST_CAP) {
+            uint8_t* S = s_row[wp];
+            for (int64_t j = b; j < e; ++j) S[j - R0] = (uint8_t)lane;
+            __syncwarp();
+            const int ns = (int)(R1 - R0);
+            for (int j0 = 0; j0 < ns; j0 += 32) {
+                const int j = j0 + lane;
+                const int bk = j < ns ? bucket(llabs((int64_t)col[R0 + j] - (pw + S[j]))) : -1;
+                // one shared atomic per bucket among the warp's lanes
+                const unsigned peers = __match_any_sync(FULL, bk);
+                if (bk >= 0 && lane == __ffs(peers) - 1) atomicAdd(&sh[bk], (unsigned)__popc(peers));
+            }
+            __syncwarp();
+        } else {
+            for (int64_t j = b; j < e; ++j) atomicAdd(&sh[bucket(llabs((int64_t)col[j] - r))], 1u);
         }
     }
     __syncthreads();
