@@ -434,7 +434,7 @@ __device__ void block_stats_rows(Acc (&s1)[E], Acc (&s2)[E], double* __restrict_
 
 
 template <typename T, int K, int U>
-__global__ void __launch_bounds__(SM_THREADS) k_sweep_row(
+__device__ __forceinline__ void sweep_row_body(
     int64_t n64, const int64_t* __restrict__ rowptr, const typename SlotOf<T>::type* __restrict__ slots,
     const T* __restrict__ Ain, T* __restrict__ Aout, double omega_d, const double* __restrict__ stats_in,
     double* __restrict__ part, unsigned* __restrict__ counter, double* __restrict__ stats_out) {
@@ -523,6 +523,25 @@ __global__ void __launch_bounds__(SM_THREADS) k_sweep_row(
         e1 = e2;
     }
     block_stats_rows<Acc, K, E, G>(s1, s2, part, counter, n64, stats_out);
+}
+
+// the registers as the compiler fits them (three blocks per SM for FP32
+// rows of 24 columns) ...
+template <typename T, int K, int U>
+__global__ void __launch_bounds__(SM_THREADS) k_sweep_row(
+    int64_t n64, const int64_t* __restrict__ rowptr, const typename SlotOf<T>::type* __restrict__ slots,
+    const T* __restrict__ Ain, T* __restrict__ Aout, double omega_d, const double* __restrict__ stats_in,
+    double* __restrict__ part, unsigned* __restrict__ counter, double* __restrict__ stats_out) {
+    sweep_row_body<T, K, U>(n64, rowptr, slots, Ain, Aout, omega_d, stats_in, part, counter, stats_out);
+}
+
+// ... or fitted to four blocks per SM (four slots in flight)
+template <typename T, int K>
+__global__ void __launch_bounds__(SM_THREADS, 4) k_sweep_row_fit4(
+    int64_t n64, const int64_t* __restrict__ rowptr, const typename SlotOf<T>::type* __restrict__ slots,
+    const T* __restrict__ Ain, T* __restrict__ Aout, double omega_d, const double* __restrict__ stats_in,
+    double* __restrict__ part, unsigned* __restrict__ counter, double* __restrict__ stats_out) {
+    sweep_row_body<T, K, 4>(n64, rowptr, slots, Ain, Aout, omega_d, stats_in, part, counter, stats_out);
 }
 
 // X = (A - mu) * inv_s, chunk-parallel; A may be X itself (each entry is read
@@ -741,20 +760,34 @@ static cudaError_t launch_sweep_row(gr_ctx* c, const SweepPlan& P, const T* Ain,
     // two slots in flight per lane; four on rows of mean degree >= 10 in
     // FP32/BF16 storage (measured: 13-19 % faster there, slower in FP64 and
     // on shorter rows).  The products are added in slot order either way.
-    static int bps2 = 0, bps4 = 0;
+    // Large blocks that stay in L2 (at least ROW_DENSE_MIN_ROWS rows, at most
+    // ROW_DENSE_MAX_BYTES) are gather-latency bound: there the four-slot
+    // kernel runs with its registers fitted to four blocks per SM (level 1 of
+    // the 128^3 mesh, 605k rows: 86 against 96 us per sweep; smaller levels
+    // ran slower with more, smaller blocks).
+    constexpr int64_t ROW_DENSE_MIN_ROWS = 400000;
+    constexpr size_t ROW_DENSE_MAX_BYTES = size_t(96) << 20;
+    static int bps2 = 0, bps4 = 0, bps4d = 0;
     if (!bps2) {
         GR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps2, k_sweep_row<T, K, 2>, SM_THREADS, 0));
         GR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps4, k_sweep_row<T, K, 4>, SM_THREADS, 0));
+        GR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps4d, k_sweep_row_fit4<T, K>, SM_THREADS, 0));
         if (bps2 < 1) bps2 = 1;
         if (bps4 < 1) bps4 = 1;
+        if (bps4d < 1) bps4d = 1;
     }
     const bool four = sizeof(T) < 8 && c->n > 0 && 2.0 * (double)c->m / (double)c->n >= 10.0;
-    int grid = c->num_sms * (four ? bps4 : bps2);
+    const bool dense = four && c->n >= ROW_DENSE_MIN_ROWS &&
+                       (size_t)c->n * K * sizeof(T) <= ROW_DENSE_MAX_BYTES;
+    int grid = c->num_sms * (dense ? bps4d : (four ? bps4 : bps2));
     if (grid > part_cap) grid = part_cap;
     const typename SlotOf<T>::type* slots;
     if constexpr (sizeof(T) == 8) slots = P.cw64;
     else slots = c->cw32;
-    if (four)
+    if (dense)
+        k_sweep_row_fit4<T, K><<<grid, SM_THREADS, 0, c->stream>>>(c->n, c->rowptr, slots, Ain, Aout, omega, st_in,
+                                                                   part, counter, st_out);
+    else if (four)
         k_sweep_row<T, K, 4><<<grid, SM_THREADS, 0, c->stream>>>(c->n, c->rowptr, slots, Ain, Aout, omega, st_in, part,
                                                                  counter, st_out);
     else

@@ -128,6 +128,25 @@ def test_sweep_kernels_large_grid(gr, oracle_mod, kind, K):
 
 
 @pytest.mark.parametrize("K", [16, 24])
+def test_row_kernel_on_a_large_l2_resident_block(gr, oracle_mod, K):
+    # 420,000 nodes of mean degree 12.5: the row-group kernel with four slots
+    # in flight and its registers fitted to four blocks per SM (a block of
+    # this size stays in L2)
+    g = W.random_sparse(420_000, 2_205_000, seed=9)
+    G = gr.graph_reduce_create(g.n, g.u, g.v, g.w)
+    S, omega, seed, level = 3, 0.7, 4, 1
+    ref = oracle_mod.smooth(g.n, g.u, g.v, g.w, K, S, omega, seed, level)
+    assert gr.graph_reduce_sweep_plan(G, K, torch.float32) == gr.GR_SWEEP_ROW
+    for dtype, bar in ((torch.float32, 1e-5), (torch.bfloat16, None)):
+        X = _smooth(gr, G, g.n, K, dtype, S, omega, seed, level)
+        if bar is not None:
+            err = _col_relerr(X.double().cpu().numpy(), ref).max()
+            assert err <= bar, (K, err)
+        else:
+            assert torch.isfinite(X.float()).all()
+
+
+@pytest.mark.parametrize("K", [16, 24])
 def test_auto_band_on_a_large_grid(gr, oracle_mod, K):
     # 200 x 1100 grid (220,000 nodes, rows 200 apart): large enough for a
     # chunk of bands per SM and banded, so the automatic choice takes the band
