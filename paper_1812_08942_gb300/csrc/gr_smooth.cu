@@ -760,8 +760,8 @@ static cudaError_t launch_sweep_row(gr_ctx* c, const SweepPlan& P, const T* Ain,
     // two slots in flight per lane; four on rows of mean degree >= 10 in
     // FP32/BF16 storage (measured: 13-19 % faster there, slower in FP64 and
     // on shorter rows).  The products are added in slot order either way.
-    // Large blocks that stay in L2 (at least ROW_DENSE_MIN_ROWS rows, at most
-    // ROW_DENSE_MAX_BYTES) are gather-latency bound: there the four-slot
+    // Large FP32 blocks that stay in L2 (at least ROW_DENSE_MIN_ROWS rows, at
+    // most ROW_DENSE_MAX_BYTES) are gather-latency bound: there the four-slot
     // kernel runs with its registers fitted to four blocks per SM (level 1 of
     // the 128^3 mesh, 605k rows: 86 against 96 us per sweep; smaller levels
     // ran slower with more, smaller blocks).
@@ -771,23 +771,29 @@ static cudaError_t launch_sweep_row(gr_ctx* c, const SweepPlan& P, const T* Ain,
     if (!bps2) {
         GR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps2, k_sweep_row<T, K, 2>, SM_THREADS, 0));
         GR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps4, k_sweep_row<T, K, 4>, SM_THREADS, 0));
-        GR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps4d, k_sweep_row_fit4<T, K>, SM_THREADS, 0));
+        if constexpr (sizeof(T) == 4)
+            GR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps4d, k_sweep_row_fit4<T, K>, SM_THREADS, 0));
         if (bps2 < 1) bps2 = 1;
         if (bps4 < 1) bps4 = 1;
         if (bps4d < 1) bps4d = 1;
     }
     const bool four = sizeof(T) < 8 && c->n > 0 && 2.0 * (double)c->m / (double)c->n >= 10.0;
-    const bool dense = four && c->n >= ROW_DENSE_MIN_ROWS &&
+    const bool dense = four && sizeof(T) == 4 && c->n >= ROW_DENSE_MIN_ROWS &&
                        (size_t)c->n * K * sizeof(T) <= ROW_DENSE_MAX_BYTES;
     int grid = c->num_sms * (dense ? bps4d : (four ? bps4 : bps2));
     if (grid > part_cap) grid = part_cap;
     const typename SlotOf<T>::type* slots;
     if constexpr (sizeof(T) == 8) slots = P.cw64;
     else slots = c->cw32;
-    if (dense)
-        k_sweep_row_fit4<T, K><<<grid, SM_THREADS, 0, c->stream>>>(c->n, c->rowptr, slots, Ain, Aout, omega, st_in,
-                                                                   part, counter, st_out);
-    else if (four)
+    if constexpr (sizeof(T) == 4) {
+        if (dense) {
+            k_sweep_row_fit4<T, K><<<grid, SM_THREADS, 0, c->stream>>>(c->n, c->rowptr, slots, Ain, Aout, omega,
+                                                                       st_in, part, counter, st_out);
+            count_launch();
+            return cudaGetLastError();
+        }
+    }
+    if (four)
         k_sweep_row<T, K, 4><<<grid, SM_THREADS, 0, c->stream>>>(c->n, c->rowptr, slots, Ain, Aout, omega, st_in, part,
                                                                  counter, st_out);
     else

@@ -130,8 +130,8 @@ def test_sweep_kernels_large_grid(gr, oracle_mod, kind, K):
 @pytest.mark.parametrize("K", [16, 24])
 def test_row_kernel_on_a_large_l2_resident_block(gr, oracle_mod, K):
     # 420,000 nodes of mean degree 12.5: the row-group kernel with four slots
-    # in flight and its registers fitted to four blocks per SM (a block of
-    # this size stays in L2)
+    # in flight, in FP32 with its registers fitted to four blocks per SM (a
+    # block of this size stays in L2), in BF16 as the compiler fits them
     g = W.random_sparse(420_000, 2_205_000, seed=9)
     G = gr.graph_reduce_create(g.n, g.u, g.v, g.w)
     S, omega, seed, level = 3, 0.7, 4, 1
