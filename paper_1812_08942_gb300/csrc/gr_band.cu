@@ -423,7 +423,6 @@ __global__ void __launch_bounds__(band_threads<T, K>(), 1) k_sweep_band(const __
     __shared__ BandMeta meta[BAND_NS];
     __shared__ int abort_flag;
     __shared__ Acc st_sh[2 * K];
-    __shared__ bool last;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
@@ -641,13 +640,7 @@ __global__ void __launch_bounds__(band_threads<T, K>(), 1) k_sweep_band(const __
     }
     __threadfence();
     __syncthreads();
-    if (tid == 0) last = atomicAdd(a.counter, 1u) == gridDim.x - 1;
-    __syncthreads();
-    if (last) {
-        __threadfence();
-        finish_stats<K, 256>(a.part, gridDim.x, a.n64, a.stats_out);
-        if (tid == 0) *a.counter = 0u;
-    }
+    finish_stats<K, 256>(a.part, gridDim.x, a.counter, a.n64, a.stats_out);
 }
 
 // ---------------------------------------------------------------------------

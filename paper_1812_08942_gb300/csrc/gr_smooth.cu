@@ -30,7 +30,6 @@ __device__ void block_stats(Acc (&s1)[E], Acc (&s2)[E], double* __restrict__ par
                             unsigned* __restrict__ counter, int64_t n,
                             double* __restrict__ stats_out) {
     __shared__ double wst[SM_WARPS][2 * K];
-    __shared__ bool last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
@@ -55,13 +54,7 @@ __device__ void block_stats(Acc (&s1)[E], Acc (&s2)[E], double* __restrict__ par
     }
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == gridDim.x - 1;
-    __syncthreads();
-    if (last) {
-        __threadfence();
-        finish_stats<K, SM_THREADS>(part, gridDim.x, n, stats_out);
-        if (threadIdx.x == 0) *counter = 0u;
-    }
+    finish_stats<K, SM_THREADS>(part, gridDim.x, counter, n, stats_out);
 }
 
 // Column sums of a stored block, per lane in the accumulator type (FP32 for
@@ -194,7 +187,8 @@ static int init_grid(const gr_ctx* c, int64_t n) {
     }
     constexpr int GP = RowLayout<T, K>::GP;
     const int64_t want = ceil_div(n, (int64_t)SM_WARPS * (32 / GP));
-    const int64_t cap = (int64_t)c->num_sms * occ;
+    int64_t cap = (int64_t)c->num_sms * occ;
+    if (cap > STATS_GROUP * STATS_MAX_GROUPS) cap = STATS_GROUP * STATS_MAX_GROUPS;
     return (int)(want < cap ? (want > 0 ? want : 1) : cap);
 }
 
@@ -393,7 +387,6 @@ template <typename Acc, int K, int E, int G>
 __device__ void block_stats_rows(Acc (&s1)[E], Acc (&s2)[E], double* __restrict__ part,
                                  unsigned* __restrict__ counter, int64_t n, double* __restrict__ stats_out) {
     __shared__ double wst[SM_WARPS][2 * K];
-    __shared__ bool last;
     constexpr int RPW = 32 / G;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // lanes q < G collect the sums of lanes q + r G (same chunk, other rows)
@@ -423,13 +416,7 @@ __device__ void block_stats_rows(Acc (&s1)[E], Acc (&s2)[E], double* __restrict_
     }
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == gridDim.x - 1;
-    __syncthreads();
-    if (last) {
-        __threadfence();
-        finish_stats<K, SM_THREADS>(part, gridDim.x, n, stats_out);
-        if (threadIdx.x == 0) *counter = 0u;
-    }
+    finish_stats<K, SM_THREADS>(part, gridDim.x, counter, n, stats_out);
 }
 
 
@@ -822,11 +809,12 @@ static cudaError_t launch_sweep(gr_ctx* c, const SweepPlan& P, const T* Ain, T* 
     return launch_sweep_row<T, K>(c, P, Ain, Aout, omega, st_in, part, part_cap, counter, st_out);
 }
 
-// Bytes of the statistics region: two 2K-double statistics sets, the
-// last-block counter and the band kernel's error word.
+// Bytes of the statistics region: two 2K-double statistics sets, then the
+// counter words (the kernel and group tickets of the statistics finish and
+// the band kernel's error word).
 template <int K>
 constexpr size_t stats_bytes() {
-    return sizeof(double) * 4 * K + 64;
+    return sizeof(double) * 4 * K + STATS_COUNTER_BYTES;
 }
 
 // X0, `sweeps` sweeps and the final centring + scaling into X.  buf is the
@@ -841,8 +829,8 @@ static cudaError_t run_sweeps(gr_ctx* c, SweepScratch& sc, int sweeps, double om
     double* st0 = stats;
     double* st1 = st0 + 2 * K;
     unsigned* counter = (unsigned*)(st1 + 2 * K);
-    // counter and error word start at zero: the region may hold an earlier call's values
-    GR_CUDA(cudaMemsetAsync(counter, 0, 2 * sizeof(unsigned), s));
+    // the tickets and the error word start at zero: the region may hold an earlier call's values
+    GR_CUDA(cudaMemsetAsync(counter, 0, STATS_COUNTER_BYTES, s));
     SweepPlan P;
     // the partials are free until k_init: scratch for the locality profile
     if (sweeps > 0) GR_CUDA((sweep_prepare<T, K>(c, sc, part_cap, part, &P)));
@@ -878,7 +866,10 @@ static cudaError_t run_sweeps(gr_ctx* c, SweepScratch& sc, int sweeps, double om
 }
 
 // blocks any sweep or k_init grid may have (the statistics partials)
-static int part_capacity(const gr_ctx* c) { return c->num_sms * 8; }
+static int part_capacity(const gr_ctx* c) {
+    const int cap = c->num_sms * 8;
+    return cap < STATS_GROUP * STATS_MAX_GROUPS ? cap : STATS_GROUP * STATS_MAX_GROUPS;
+}
 
 template <typename T, int K>
 static cudaError_t run_smooth(gr_ctx* c, int sweeps, double omega, uint64_t seed, int level,
@@ -913,13 +904,13 @@ static cudaError_t run_test_vectors(gr_ctx* c, uint64_t seed, int level, T* X) {
     cudaStream_t s = c->stream;
     const int64_t n = c->n;
     void *p_st, *p_part;
-    GR_CUDA(c->ws.get(WS_SMOOTH_STATS, sizeof(double) * 4 * K + 64, &p_st));
+    GR_CUDA(c->ws.get(WS_SMOOTH_STATS, stats_bytes<K>(), &p_st));
     double* st0 = (double*)p_st;
     unsigned* counter = (unsigned*)(st0 + 4 * K);
-    const int64_t cap = (int64_t)c->num_sms * 8;
+    const int64_t cap = part_capacity(c);
     const int igrid = init_grid<T, K>(c, n);
     GR_CUDA(c->ws.get(WS_SMOOTH_PART, sizeof(double) * 2 * K * (size_t)cap, &p_part));
-    GR_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned), s));
+    GR_CUDA(cudaMemsetAsync(counter, 0, STATS_COUNTER_BYTES, s));
     k_init<T, K><<<igrid, SM_THREADS, 0, s>>>(n, seed, (uint64_t)level, X, (double*)p_part, counter, st0);
     count_launch();
     return cudaGetLastError();
@@ -1241,13 +1232,13 @@ static gr_status run_smooth_gs(gr_ctx* c, int sweeps, double omega, uint64_t see
     const int64_t n = c->n;
     constexpr int G = RowLayout<T, K>::G;
     void *p_st, *p_part;
-    GR_TRY_CUDA(c, c->ws.get(WS_SMOOTH_STATS, sizeof(double) * 4 * K + 64, &p_st), "scratch");
+    GR_TRY_CUDA(c, c->ws.get(WS_SMOOTH_STATS, stats_bytes<K>(), &p_st), "scratch");
     double* st = (double*)p_st;
     unsigned* counter = (unsigned*)(st + 4 * K);
     const int igrid = init_grid<T, K>(c, n);
     GR_TRY_CUDA(c, c->ws.get(WS_SMOOTH_PART, sizeof(double) * 2 * K * (size_t)igrid, &p_part), "scratch");
     double* part = (double*)p_part;
-    GR_TRY_CUDA(c, cudaMemsetAsync(counter, 0, sizeof(unsigned), s), "memset");
+    GR_TRY_CUDA(c, cudaMemsetAsync(counter, 0, STATS_COUNTER_BYTES, s), "memset");
     const typename SlotOf<T>::type* slots;
     if constexpr (sizeof(T) == 8) {
         if (!c->cw64) {
