@@ -29,30 +29,45 @@ __global__ void k_prolong(int64_t n, int k, const int32_t* __restrict__ map, con
     Uf[idx] = Uc[(int64_t)map[i] * k + c];
 }
 
-// One weighted-Jacobi iteration on (L - lambda_c B) y = 0 for every column c,
-// thread per (row, column): y <- (1 - w) y + w (A y)_r / (D_r - lambda_c B_r),
+// Weighted-Jacobi iteration on (L - lambda_c B) y = 0 for every column c:
+//   y <- (1 - w) y + w (A y)_r / (D_r - lambda_c B_r),
 // with (A y)_r = D_r (D^-1 A y)_r from the row-scaled weights and B the
 // diagonal mass b (NULL: B = I); a row whose shifted diagonal is not positive
-// keeps its value.
+// keeps its value.  The gain g_rc = w D_r / (D_r - lambda_c B_r) depends only
+// on the level, so it is computed once per level (g = -1: the row keeps its
+// value; otherwise g >= 0) and an
+// iteration is y <- (1 - w) y + g (D^-1 A y)_r: FP64 is a small fraction of
+// the FP32 rate on this part, and the division, taken per entry and
+// iteration, cost more than the row's products.
+__global__ void k_shift_gain(int64_t n, int k, const double* __restrict__ deg, const double* __restrict__ lam,
+                             const double* __restrict__ b, double omega, double* __restrict__ g) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * k) return;
+    const int64_t r = idx / k;
+    const int c = (int)(idx % k);
+    const double D = deg[r];
+    const double diag = D - lam[c] * (b ? b[r] : 1.0);
+    g[idx] = diag > 0.0 ? omega * D / diag : -1.0;
+}
+
+// One iteration, thread per (row, column).
 __global__ void k_shifted_jacobi(int64_t n, int k, const int64_t* __restrict__ rowptr,
                                  const int32_t* __restrict__ col, const double* __restrict__ wn64,
-                                 const double* __restrict__ deg, const double* __restrict__ lam,
-                                 const double* __restrict__ b, double omega, const double* __restrict__ Yin,
+                                 const double* __restrict__ gain, double omega, const double* __restrict__ Yin,
                                  double* __restrict__ Yout) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= n * k) return;
     const int64_t r = idx / k;
     const int c = (int)(idx % k);
     const double y = Yin[idx];
-    const double D = deg[r];
-    const double diag = D - lam[c] * (b ? b[r] : 1.0);
-    if (!(diag > 0.0)) {
+    const double g = gain[idx];
+    if (g < 0.0) {
         Yout[idx] = y;
         return;
     }
     double s = 0.0;
     for (int64_t j = rowptr[r]; j < rowptr[r + 1]; ++j) s += wn64[j] * Yin[(int64_t)col[j] * k + c];
-    Yout[idx] = (1.0 - omega) * y + omega * (s * D / diag);
+    Yout[idx] = fma(g, s, (1.0 - omega) * y);
 }
 
 // The same iteration with G lanes per row, each holding one 16-byte chunk
@@ -62,15 +77,10 @@ template <int K>
 __global__ void __launch_bounds__(ET) k_shifted_jacobi_rows(int64_t n64, const int64_t* __restrict__ rowptr,
                                                            const int32_t* __restrict__ col,
                                                            const double* __restrict__ wn64,
-                                                           const double* __restrict__ deg,
-                                                           const double* __restrict__ lam_in,
-                                                           const double* __restrict__ b, double omega,
+                                                           const double* __restrict__ gain, double omega,
                                                            const double* __restrict__ Yin,
                                                            double* __restrict__ Yout) {
     constexpr int E = K >= 2 ? 2 : 1, G = K / E, RPW = 32 / G;
-    __shared__ double lam[K];
-    if (threadIdx.x < K) lam[threadIdx.x] = lam_in[threadIdx.x];
-    __syncthreads();
     const int64_t n = n64;
     const int lane = threadIdx.x & 31, seg = lane / G, q = lane % G;
     if (seg >= RPW) return;
@@ -101,14 +111,12 @@ __global__ void __launch_bounds__(ET) k_shifted_jacobi_rows(int64_t n64, const i
                 if (two) acc[0] = fma(w1, x1, acc[0]);
             }
         }
-        const double D = deg[r];
-        const double br = b ? b[r] : 1.0;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             const int c = q * E + e;
             const double y = Yin[r * K + c];
-            const double diag = D - lam[c] * br;
-            Yout[r * K + c] = diag > 0.0 ? (1.0 - omega) * y + omega * (acc[e] * D / diag) : y;
+            const double g = gain[r * K + c];
+            Yout[r * K + c] = g >= 0.0 ? fma(g, acc[e], (1.0 - omega) * y) : y;
         }
     }
 }
@@ -236,6 +244,7 @@ gr_status eigensolve_impl(gr_ctx* const* levels, int nlevels, int k, int normali
         return off;
     };
     const size_t o_Y0 = add(sizeof(double) * (size_t)nmax * k), o_Y1 = add(sizeof(double) * (size_t)nmax * k),
+                 o_G = add(sizeof(double) * (size_t)nmax * k),
                  o_V = add(sizeof(double) * (size_t)n0 * k), o_T = add(sizeof(double) * (size_t)n0),
                  o_part = add(sizeof(double) * (size_t)RB), o_sc = add(sizeof(double) * 64),
                  o_lam = add(sizeof(double) * 32), o_ctr = add(64);
@@ -248,6 +257,7 @@ gr_status eigensolve_impl(gr_ctx* const* levels, int nlevels, int k, int normali
     GR_TRY_CUDA(f, f->ws.get(WS_EIG, need, &base), "eigensolver scratch");
     char* Bp = (char*)base;
     double* Y[2] = {(double*)(Bp + o_Y0), (double*)(Bp + o_Y1)};
+    double* gain = (double*)(Bp + o_G);
     double* V = (double*)(Bp + o_V);
     double* T = (double*)(Bp + o_T);
     double* part = (double*)(Bp + o_part);
@@ -287,11 +297,14 @@ gr_status eigensolve_impl(gr_ctx* const* levels, int nlevels, int k, int normali
         k_prolong<<<blocks(n * k), ET, 0, s>>>(n, k, levels[l + 1]->parent_map, Y[cur], Y[cur ^ 1]);
         count_launch();
         cur ^= 1;
+        if (iters > 0) {
+            k_shift_gain<<<blocks(n * k), ET, 0, s>>>(n, k, g->deg, lam, mass[l], omega, gain);
+            count_launch();
+        }
         for (int it = 0; it < iters; ++it) {
             const unsigned gr = (unsigned)(f->num_sms * 8);
-#define GR_SJ_ROWS(KK)                                                                                      \
-    k_shifted_jacobi_rows<KK><<<gr, ET, 0, s>>>(n, g->rowptr, g->col, g->wn64, g->deg, lam, mass[l], omega, \
-                                                Y[cur], Y[cur ^ 1])
+#define GR_SJ_ROWS(KK)                                                                                    \
+    k_shifted_jacobi_rows<KK><<<gr, ET, 0, s>>>(n, g->rowptr, g->col, g->wn64, gain, omega, Y[cur], Y[cur ^ 1])
             switch (k) {
                 case 2: GR_SJ_ROWS(2); break;
                 case 4: GR_SJ_ROWS(4); break;
@@ -299,8 +312,8 @@ gr_status eigensolve_impl(gr_ctx* const* levels, int nlevels, int k, int normali
                 case 16: GR_SJ_ROWS(16); break;
                 case 32: GR_SJ_ROWS(32); break;
                 default:
-                    k_shifted_jacobi<<<blocks(n * k), ET, 0, s>>>(n, k, g->rowptr, g->col, g->wn64, g->deg, lam,
-                                                                mass[l], omega, Y[cur], Y[cur ^ 1]);
+                    k_shifted_jacobi<<<blocks(n * k), ET, 0, s>>>(n, k, g->rowptr, g->col, g->wn64, gain, omega,
+                                                                Y[cur], Y[cur ^ 1]);
             }
 #undef GR_SJ_ROWS
             count_launch();
