@@ -35,10 +35,12 @@ __global__ void k_prolong(int64_t n, int k, const int32_t* __restrict__ map, con
 // diagonal mass b (NULL: B = I); a row whose shifted diagonal is not positive
 // keeps its value.  The gain g_rc = w D_r / (D_r - lambda_c B_r) depends only
 // on the level, so it is computed once per level (g = -1: the row keeps its
-// value; otherwise g >= 0) and an
-// iteration is y <- (1 - w) y + g (D^-1 A y)_r: FP64 is a small fraction of
-// the FP32 rate on this part, and the division, taken per entry and
-// iteration, cost more than the row's products.
+// value; otherwise g >= 0) and an iteration is
+//   y <- (1 - w) y + g (D^-1 A y)_r:
+// FP64 runs at a small fraction of the FP32 rate on this part, and the
+// division, taken per entry and iteration, cost more than the row's
+// products.  The keep test reads the sign bit of g with an integer compare
+// (a floating compare would take the FP64 pipe too).
 __global__ void k_shift_gain(int64_t n, int k, const double* __restrict__ deg, const double* __restrict__ lam,
                              const double* __restrict__ b, double omega, double* __restrict__ g) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -61,7 +63,7 @@ __global__ void k_shifted_jacobi(int64_t n, int k, const int64_t* __restrict__ r
     const int c = (int)(idx % k);
     const double y = Yin[idx];
     const double g = gain[idx];
-    if (g < 0.0) {
+    if (__double2hiint(g) < 0) {
         Yout[idx] = y;
         return;
     }
@@ -116,7 +118,7 @@ __global__ void __launch_bounds__(ET) k_shifted_jacobi_rows(int64_t n64, const i
             const int c = q * E + e;
             const double y = Yin[r * K + c];
             const double g = gain[r * K + c];
-            Yout[r * K + c] = g >= 0.0 ? fma(g, acc[e], (1.0 - omega) * y) : y;
+            Yout[r * K + c] = __double2hiint(g) >= 0 ? fma(g, acc[e], (1.0 - omega) * y) : y;
         }
     }
 }
