@@ -140,6 +140,51 @@ __device__ __forceinline__ float uniform_pm1<__nv_bfloat16>(uint64_t z) {
     return uniform_pm1<float>(z);
 }
 
+// Block-level combine when thread t of the grid holds the sums of column
+// chunk (t mod G) -- the grid's thread count is a multiple of G, so lane l of
+// a warp holds chunk (c + l) mod G with c the warp's first thread: lane l < G
+// adds the lanes l + r G (all 32 lanes carry data) and writes its chunk's
+// sums.  Then as block_stats.
+template <typename Acc, int K, int E, int G>
+__device__ void block_stats_chunks(Acc (&s1)[E], Acc (&s2)[E], int q, double* __restrict__ part,
+                                   unsigned* __restrict__ counter, int64_t n, double* __restrict__ stats_out) {
+    __shared__ double wst[SM_WARPS][2 * K];
+    constexpr int RW = (32 + G - 1) / G;  // lane groups per warp
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+#pragma unroll
+        for (int r = 1; r < RW; ++r) {
+            const int src = lane + r * G;
+            const Acc a1 = __shfl_sync(0xffffffffu, s1[e], src & 31);
+            const Acc a2 = __shfl_sync(0xffffffffu, s2[e], src & 31);
+            if (lane < G && src < 32) {
+                s1[e] += a1;
+                s2[e] += a2;
+            }
+        }
+    if (lane < G) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            wst[warp][q * E + e] = (double)s1[e];
+            wst[warp][K + q * E + e] = (double)s2[e];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 * K) {
+        double t = 0.0;
+        for (int w = 0; w < SM_WARPS; ++w) t += wst[w][threadIdx.x];
+        part[(int64_t)blockIdx.x * 2 * K + threadIdx.x] = t;
+    }
+    __threadfence();
+    __syncthreads();
+    finish_stats<K, SM_THREADS>(part, gridDim.x, counter, n, stats_out);
+}
+
+// X0 and its statistics.  Chunk c (entries c E ... c E + E - 1 of the
+// row-major block, row c / G) goes to thread c mod T of the grid, T threads in
+// all, a multiple of G (init_grid): every lane of a warp works, and each
+// thread keeps one chunk column.
 template <typename T, int K>
 __global__ void __launch_bounds__(SM_THREADS) k_init(int64_t n, uint64_t seed, uint64_t level,
                                                      T* __restrict__ A, double* __restrict__ part,
@@ -147,32 +192,28 @@ __global__ void __launch_bounds__(SM_THREADS) k_init(int64_t n, uint64_t seed, u
                                                      double* __restrict__ stats_out) {
     using L = RowLayout<T, K>;
     using Acc = typename AccOf<T>::type;
-    constexpr int E = L::E, G = L::G, GP = L::GP;
-    constexpr int RPW = 32 / GP;
-    const int lane = threadIdx.x & 31;
-    const int q = lane % GP, seg = lane / GP;
+    constexpr int E = L::E, G = L::G;
+    const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t c0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t total = (uint64_t)n * G;
+    const int q = (int)(c0 % G);
     Acc s1[E], s2[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) s1[e] = s2[e] = Acc(0);
-    const int64_t warp_global = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t r0 = warp_global * RPW; r0 < n; r0 += nwarps * RPW) {
-        int64_t row = r0 + seg;
-        if (row < n && q < G) {
-            Acc x[E];
-            // generator state of this chunk's first entry; the next entries
-            // follow by one gamma each
-            uint64_t zs = seed + ((level << 40) + (uint64_t)row * K + (uint64_t)(q * E) + 1ull) * SM_GAMMA;
+    for (uint64_t c = c0; c < total; c += nthreads) {
+        Acc x[E];
+        // generator state of this chunk's first entry (entry index c E); the
+        // next entries follow by one gamma each
+        uint64_t zs = seed + ((level << 40) + c * E + 1ull) * SM_GAMMA;
 #pragma unroll
-            for (int e = 0; e < E; ++e) {
-                x[e] = uniform_pm1<T>(splitmix64_mix(zs));
-                zs += SM_GAMMA;
-            }
-            store_chunk<T, E>(A + row * K + q * E, x);
-            add_sums<Acc, E>(s1, s2, x);
+        for (int e = 0; e < E; ++e) {
+            x[e] = uniform_pm1<T>(splitmix64_mix(zs));
+            zs += SM_GAMMA;
         }
+        store_chunk<T, E>(A + c * E, x);
+        add_sums<Acc, E>(s1, s2, x);
     }
-    block_stats<Acc, K, E, G, GP>(s1, s2, part, counter, n, stats_out);
+    block_stats_chunks<Acc, K, E, G>(s1, s2, q, part, counter, n, stats_out);
 }
 
 // k_init's grid: one full wave of resident blocks (a larger grid would leave
@@ -185,11 +226,16 @@ static int init_grid(const gr_ctx* c, int64_t n) {
             occ = 1;
         if (occ > 8) occ = 8;
     }
-    constexpr int GP = RowLayout<T, K>::GP;
-    const int64_t want = ceil_div(n, (int64_t)SM_WARPS * (32 / GP));
+    // the grid's thread count must be a multiple of G: of 3 blocks when 3 | G
+    constexpr int G = RowLayout<T, K>::G;
+    constexpr int64_t step = G % 3 == 0 ? 3 : 1;
+    const int64_t want = ceil_div(n * G, (int64_t)SM_THREADS);
     int64_t cap = (int64_t)c->num_sms * occ;
     if (cap > STATS_GROUP * STATS_MAX_GROUPS) cap = STATS_GROUP * STATS_MAX_GROUPS;
-    return (int)(want < cap ? (want > 0 ? want : 1) : cap);
+    int64_t g = want < cap ? want : cap;
+    g = (g + step - 1) / step * step;
+    if (g > cap) g -= step;
+    return (int)(g > 0 ? g : step);
 }
 
 // ---------------------------------------------------------------------------
